@@ -1,0 +1,253 @@
+"""FP64 CPU oracle of the coupled D2Q9 pseudopotential + D2Q5 thermal LBM step.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It wraps ``lbm_oracle.c`` (plain C, double precision) through ctypes
+and shares no code with the CUDA library in ``paper_2205_00686_gb300``.
+
+The pins that tie this oracle to the paper live in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_HDR = os.path.join(_HERE, "lbm_oracle.h")
+LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
+
+PERIODIC, WALL, OPEN = 0, 1, 2
+T_PERIODIC, T_DIRICHLET, T_ADIABATIC = 0, 1, 2
+EDGE_W, EDGE_E, EDGE_S, EDGE_N = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    tmp = LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC",
+           "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "a", "b", "R", "omega", "G", "sigma", "nu", "s0", "s_e", "s_eps", "s_j", "s_q",
+        "lambda_", "cv", "w_dot", "vs0", "vs3", "vs4", "gravity")] + [
+        ("frozen_flow", ctypes.c_int), ("frozen_thermal", ctypes.c_int)]
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("flow", ctypes.c_int * 4), ("therm", ctypes.c_int * 4),
+                ("T_edge", ctypes.c_double * 4), ("theta_deg", ctypes.c_double),
+                ("heater_x0", ctypes.c_int), ("heater_x1", ctypes.c_int),
+                ("T_heater", ctypes.c_double)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "mass", "energy", "liquid_mass", "liquid_area", "liquid_area_smooth",
+        "diameter", "diameter_smooth", "max_u")] + [
+        ("step", ctypes.c_long), ("nonfinite", ctypes.c_int)]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB_PATH)
+        P, B = ctypes.POINTER(Params), ctypes.POINTER(BC)
+        L.orc_Tc.restype = ctypes.c_double
+        L.orc_Tc.argtypes = [P]
+        for fn in ("orc_p_eos", "orc_dpdT", "orc_psi2"):
+            getattr(L, fn).restype = ctypes.c_double
+            getattr(L, fn).argtypes = [P, ctypes.c_double, ctypes.c_double]
+        L.orc_maxwell.argtypes = [P, ctypes.c_double, _dp, _dp]
+        L.orc_feq.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
+        L.orc_meq.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
+        L.orc_geq.argtypes = [P, ctypes.c_double, _dp]
+        L.orc_matrices.argtypes = [_dp, _dp, _dp, _dp]
+        L.orc_set_defaults.argtypes = [P]
+        L.orc_create.restype = ctypes.c_void_p
+        L.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, P, B, ctypes.POINTER(ctypes.c_int)]
+        L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_init.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
+        L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_fields.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
+        L.orc_get_populations.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+        L.orc_set_populations.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_long,
+                                          ctypes.c_double]
+        L.orc_step_count.restype = ctypes.c_long
+        L.orc_step_count.argtypes = [ctypes.c_void_p]
+        L.orc_diagnostics.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, ctypes.POINTER(Diag)]
+        L.orc_last_error.argtypes = [ctypes.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def make_params(d: dict) -> Params:
+    p = Params()
+    lib().orc_set_defaults(ctypes.byref(p))
+    for k, v in d.items():
+        name = "lambda_" if k == "lambda" else k
+        if any(name == f[0] for f in Params._fields_):
+            setattr(p, name, v)
+    return p
+
+
+def make_bc(d: dict) -> BC:
+    b = BC()
+    for e in range(4):
+        b.flow[e] = int(d["flow"][e])
+        b.therm[e] = int(d["therm"][e])
+        b.T_edge[e] = float(d.get("T_edge", (0.0,) * 4)[e])
+    b.theta_deg = float(d.get("theta_deg", 90.0))
+    b.heater_x0 = int(d.get("heater_x0", 0))
+    b.heater_x1 = int(d.get("heater_x1", 0))
+    b.T_heater = float(d.get("T_heater", 0.0))
+    return b
+
+
+# ---- closed forms -------------------------------------------------------
+
+def Tc(params: dict) -> float:
+    return lib().orc_Tc(ctypes.byref(make_params(params)))
+
+
+def p_eos(params: dict, rho: float, T: float) -> float:
+    return lib().orc_p_eos(ctypes.byref(make_params(params)), rho, T)
+
+
+def dpdT(params: dict, rho: float, T: float) -> float:
+    return lib().orc_dpdT(ctypes.byref(make_params(params)), rho, T)
+
+
+def psi2(params: dict, rho: float, T: float) -> float:
+    return lib().orc_psi2(ctypes.byref(make_params(params)), rho, T)
+
+
+def maxwell(params: dict, T: float):
+    rg, rl = ctypes.c_double(), ctypes.c_double()
+    rc = lib().orc_maxwell(ctypes.byref(make_params(params)), T, ctypes.byref(rg),
+                           ctypes.byref(rl))
+    if rc:
+        raise ValueError("no coexistence at T=%g" % T)
+    return rg.value, rl.value
+
+
+def feq(rho: float, ux: float, uy: float) -> np.ndarray:
+    out = np.zeros(9)
+    lib().orc_feq(rho, ux, uy, _ptr(out))
+    return out
+
+
+def meq(rho: float, ux: float, uy: float) -> np.ndarray:
+    out = np.zeros(9)
+    lib().orc_meq(rho, ux, uy, _ptr(out))
+    return out
+
+
+def geq(params: dict, T: float) -> np.ndarray:
+    out = np.zeros(5)
+    lib().orc_geq(ctypes.byref(make_params(params)), T, _ptr(out))
+    return out
+
+
+def matrices():
+    M, Mi, Mh, Mhi = np.zeros(81), np.zeros(81), np.zeros(25), np.zeros(25)
+    lib().orc_matrices(_ptr(M), _ptr(Mi), _ptr(Mh), _ptr(Mhi))
+    return M.reshape(9, 9), Mi.reshape(9, 9), Mh.reshape(5, 5), Mhi.reshape(5, 5)
+
+
+# ---- simulation ----------------------------------------------------------
+
+class OracleError(RuntimeError):
+    def __init__(self, code):
+        super().__init__("oracle error %d" % code)
+        self.code = code
+
+
+class Sim:
+    """One FP64 CPU simulation of an nx x ny domain."""
+
+    def __init__(self, nx: int, ny: int, params: dict, bc: dict):
+        self.nx, self.ny = nx, ny
+        self._p = make_params(params)
+        self._b = make_bc(bc)
+        err = ctypes.c_int(0)
+        self._h = lib().orc_create(nx, ny, ctypes.byref(self._p), ctypes.byref(self._b),
+                                   ctypes.byref(err))
+        if not self._h:
+            raise OracleError(err.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().orc_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def init(self, rho, ux, uy, T):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.ny, self.nx)
+                for a in (rho, ux, uy, T)]
+        rc = lib().orc_init(self._h, *[_ptr(a) for a in arrs])
+        if rc:
+            raise OracleError(rc)
+
+    def step(self, n: int = 1, check: bool = True) -> int:
+        rc = lib().orc_step(self._h, int(n))
+        if rc and check:
+            raise OracleError(rc)
+        return rc
+
+    @property
+    def step_count(self) -> int:
+        return lib().orc_step_count(self._h)
+
+    def fields(self):
+        out = [np.zeros((self.ny, self.nx)) for _ in range(4)]
+        lib().orc_fields(self._h, *[_ptr(a) for a in out])
+        return tuple(out)
+
+    def populations(self):
+        f = np.zeros((9, self.ny, self.nx))
+        g = np.zeros((5, self.ny, self.nx))
+        P = np.zeros((self.ny, self.nx))
+        lib().orc_get_populations(self._h, _ptr(f), _ptr(g), _ptr(P))
+        return f, g, P
+
+    def set_populations(self, f, g, P, step: int, rho_ave_prev: float):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        rc = lib().orc_set_populations(self._h, _ptr(f), _ptr(g), _ptr(P), int(step),
+                                       float(rho_ave_prev))
+        if rc:
+            raise OracleError(rc)
+
+    def diagnostics(self, rho_l: float, rho_g: float, sessile: bool = False) -> dict:
+        d = Diag()
+        lib().orc_diagnostics(self._h, rho_l, rho_g, int(sessile), ctypes.byref(d))
+        return {k: getattr(d, k) for k, _ in Diag._fields_}
+
+    @property
+    def last_error(self) -> int:
+        return lib().orc_last_error(self._h)

@@ -1,0 +1,112 @@
+/*
+ * FP64 CPU oracle for the coupled time step of the thermal lattice Boltzmann
+ * model for liquid-vapor phase change (Wang, Huang & He, arXiv 2205.00686).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the slow, plain reference that the
+ * CUDA path is checked against.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load it; the product path never does.  It
+ * shares no code, header, table or helper with the CUDA library.
+ *
+ * Every field array is row-major [ny][nx] (x fastest), node (0,0) at the
+ * south-west corner.  Populations are [q][ny][nx].  Everything is double.
+ *
+ * Parity status per function (see the header of lbm_oracle.c for the pins):
+ *   all functions declared here are pinned by tests in tests/test_oracle_*.py.
+ */
+#ifndef LBM_ORACLE_H
+#define LBM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* edge indices */
+#define ORC_W 0
+#define ORC_E 1
+#define ORC_S 2
+#define ORC_N 3
+
+/* flow boundary kinds */
+#define ORC_PERIODIC 0
+#define ORC_WALL 1
+#define ORC_OPEN 2
+
+/* thermal boundary kinds */
+#define ORC_T_PERIODIC 0
+#define ORC_T_DIRICHLET 1
+#define ORC_T_ADIABATIC 2
+
+/* error codes */
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENOMEM (-2)
+#define ORC_ENONFINITE (-3)
+#define ORC_EPSI (-4)
+
+typedef struct {
+    /* Peng-Robinson EOS (Section 2): a, b, gas constant R, acentric factor */
+    double a, b, R, omega;
+    /* interaction strength G and the Li forcing parameter sigma (Section 2) */
+    double G, sigma;
+    /* kinematic viscosity -> s_p; the other D2Q9 rates */
+    double nu, s0, s_e, s_eps, s_j, s_q;
+    /* thermal conductivity lambda -> varsigma_1 = varsigma_2; c_v; w_dot */
+    double lambda, cv, w_dot;
+    /* the other D2Q5 rates varsigma_0, varsigma_3, varsigma_4 */
+    double vs0, vs3, vs4;
+    /* gravity magnitude g, body force (rho - rho_ave)(0, -g) (Section 4.3) */
+    double gravity;
+    /* test hook: u == 0 and rho fixed, only the thermal lattice advances */
+    int frozen_flow;
+    /* isothermal hook: g is left unchanged, only the flow lattice advances */
+    int frozen_thermal;
+} orc_params;
+
+typedef struct {
+    int flow[4];        /* ORC_PERIODIC / ORC_WALL / ORC_OPEN per edge W,E,S,N */
+    int therm[4];       /* ORC_T_* per edge */
+    double T_edge[4];   /* wall / Dirichlet temperature per edge */
+    double theta_deg;   /* equilibrium contact angle of walls (Section 3.3) */
+    int heater_x0, heater_x1;   /* heater segment [x0,x1) on the south edge */
+    double T_heater;
+} orc_bc;
+
+typedef struct {
+    double mass, energy, liquid_mass, liquid_area, liquid_area_smooth;
+    double diameter, diameter_smooth, max_u;
+    long step;
+    int nonfinite;
+} orc_diag;
+
+typedef struct orc_sim orc_sim;
+
+/* derived constants and closed forms ---------------------------------- */
+double orc_Tc(const orc_params* p);
+double orc_p_eos(const orc_params* p, double rho, double T);
+double orc_dpdT(const orc_params* p, double rho, double T);
+double orc_psi2(const orc_params* p, double rho, double T);
+int orc_maxwell(const orc_params* p, double T, double* rho_g, double* rho_l);
+void orc_feq(double rho, double ux, double uy, double f[9]);
+void orc_geq(const orc_params* p, double T, double g[5]);
+void orc_matrices(double M[81], double Minv[81], double Mh[25], double Mhinv[25]);
+void orc_meq(double rho, double ux, double uy, double meq[9]);
+void orc_set_defaults(orc_params* p);
+
+/* simulation ----------------------------------------------------------- */
+orc_sim* orc_create(int nx, int ny, const orc_params* p, const orc_bc* bc, int* err);
+void orc_destroy(orc_sim* s);
+int orc_init(orc_sim* s, const double* rho, const double* ux, const double* uy,
+             const double* T);
+int orc_step(orc_sim* s, int n);
+int orc_fields(orc_sim* s, double* rho, double* ux, double* uy, double* T);
+int orc_get_populations(const orc_sim* s, double* f, double* g, double* P);
+int orc_set_populations(orc_sim* s, const double* f, const double* g, const double* P,
+                        long step, double rho_ave_prev);
+long orc_step_count(const orc_sim* s);
+int orc_diagnostics(orc_sim* s, double rho_l, double rho_g, int sessile, orc_diag* d);
+int orc_last_error(const orc_sim* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
