@@ -1,0 +1,359 @@
+"""Benchmark of the coupled D2Q9 pseudopotential + D2Q5 thermal LBM step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: the droplet-evaporation setup (open outflow, Dirichlet T = 0.95 T_c
+on all edges, droplet at 0.86 T_c; Section 4.1 shape) on a 4096 x 4096
+domain in FP32 -- the size the HBM-roofline target is stated on.  One step is
+one coupled update of every node.  The state (2 x 1 GiB ping-pong buffers) is
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line: MLUPS (whole job), HBM roofline of the fused step
+kernel, the end-to-end figure through the C ABI with host buffers, clocks,
+the FP64 figure, each precision's error against the FP64 CPU oracle, and the
+oracle itself timed on the host cores as a baseline.
+
+Under torchrun (N > 1) every rank advances its own replica of the domain
+(the domains are independent: replicas, weak scaling) and rank 0 reports
+the aggregate over the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 4096
+BYTES_PER_NODE = {"fp32": 120, "fp64": 240, "fp32_g16": 100}
+METRIC = "coupled D2Q9+D2Q5 MLUPS and % of HBM roofline, FP32 vs FP64 at stated error"
+STEP_SOURCES = ["paper_2205_00686_gb300/csrc/lbm_step.cu",
+                "paper_2205_00686_gb300/csrc/lbm_internal.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def step_source_hash():
+    h = hashlib.sha256()
+    for p in STEP_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sms, mx, reasons, pw = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sms)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms), "power_w_max": max(pw) if pw else None}
+
+
+def make_case(n=NX):
+    from paper_2205_00686_gb300 import workloads as W
+    return W.open_evaporation(n, n, R=640.0 * n / 4096.0, steps=0)
+
+
+def cpu_baseline(sample_n=1024, sample_steps=12):
+    """The FP64 C oracle, single-threaded, on a bounded sample of the
+    workload (a sample_n^2 domain of the same setup)."""
+    import oracle
+    c = make_case(sample_n)
+    s = oracle.Sim(c.nx, c.ny, c.params, c.bc)
+    s.init(*c.fields())
+    s.step(1)
+    t0 = time.perf_counter()
+    s.step(sample_steps)
+    dt = time.perf_counter() - t0
+    mlups = c.nx * c.ny * sample_steps / dt / 1e6
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%dx%d of the same setup, %d FP64 steps, %.1f s" % (
+                c.nx, c.ny, sample_steps, dt)}
+
+
+def accuracy_check():
+    """Each precision against the FP64 oracle: 64x64 droplet, 1000 steps."""
+    import oracle
+    import paper_2205_00686_gb300 as lbm
+    from paper_2205_00686_gb300 import workloads as W
+    c = W.static_droplet()
+    o = oracle.Sim(c.nx, c.ny, c.params, c.bc)
+    o.init(*c.fields())
+    o.step(1000)
+    ref = o.fields()
+    out = {}
+    for prec in ("fp64", "fp32", "fp32_g16"):
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec=prec)
+        d.init_fields(*c.fields())
+        d.step(1000)
+        got = d.get_rho_u_T()
+        out[prec] = max(float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(got, ref))
+        d.close()
+    return {"case": "64x64 droplet, 1000 steps, max relative field error vs FP64 oracle",
+            **{k: float("%.3e" % v) for k, v in out.items()}}
+
+
+def time_device(dom, steps, warmup, stream, torch, dist, world):
+    dom.step(warmup)
+    dom.sync()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    dom.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    dom.sync()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def run_ours(args):
+    import torch
+    import paper_2205_00686_gb300 as lbm
+    from paper_2205_00686_gb300 import _build
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world > 1:
+        _build.build()
+    stream = torch.cuda.Stream()
+    case = make_case()
+    N = case.nx * case.ny
+
+    dom = lbm.Domain(case.nx, case.ny, case.params, case.bc, prec="fp32",
+                     stream=stream.cuda_stream)
+    dom.init_fields(*case.fields())
+    with ClockSampler(local) as clk:
+        t = time_device(dom, args.steps, args.warmup, stream, torch, dist, world)
+    if world > 1:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    mlups = world * N * args.steps / t / 1e6
+    ms_per_step = t / args.steps * 1e3
+
+    # end to end through the C ABI with pinned host buffers: upload the
+    # fields, advance, read the fields back
+    pinned = [torch.from_numpy(np.ascontiguousarray(a, np.float64)).pin_memory()
+              for a in case.fields()]
+    outs = [torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    e2e_steps = args.steps
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dom.init_fields(*pinned)
+    dom.step(e2e_steps)
+    dom.get_rho_u_T(tuple(outs))
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e = {"value": round(world * N * e2e_steps / te / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": int(4 * N * 8 / e2e_steps),
+           "d2h_bytes_per_step": int(4 * N * 8 / e2e_steps),
+           "call": "lbm_init_fields(host) + lbm_step(%d) + lbm_get_rho_u_T(host)" % e2e_steps}
+
+    peak, peak_kind = measured_peaks()
+    algo = BYTES_PER_NODE["fp32"] * N
+    achieved = algo / (t / args.steps) / 1e9   # per GPU: each rank steps its own domain
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as fh:
+            tr = json.load(fh)
+        if tr.get("source_hash") == step_source_hash() and tr.get("prec") == "fp32":
+            traffic = tr.get("bytes_per_launch_4096")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_kind": "%s hbm_gbs (copy)" % peak_kind,
+                "algorithmic_bytes_per_node": BYTES_PER_NODE["fp32"],
+                "kernel": "lbm::k_step<1,%d>" % dom.tile()[0]}
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        d64 = lbm.Domain(case.nx, case.ny, case.params, case.bc, prec="fp64",
+                         stream=stream.cuda_stream)
+        d64.init_fields(*case.fields())
+        k64 = max(20, args.steps // 10)
+        t64 = time_device(d64, k64, 3, stream, torch, None, 1)
+        m64 = N * k64 / t64 / 1e6
+        extras["fp64"] = {"value": round(m64, 1), "unit": "MLUPS",
+                          "hbm_frac_of_measured": round(BYTES_PER_NODE["fp64"] * N / (t64 / k64) / 1e9 / peak, 4),
+                          "steps": k64}
+        d64.close()
+        dg = lbm.Domain(case.nx, case.ny, case.params, case.bc, prec="fp32_g16",
+                        stream=stream.cuda_stream)
+        dg.init_fields(*case.fields())
+        tg = time_device(dg, args.steps, 3, stream, torch, None, 1)
+        extras["fp32_g16"] = {"value": round(N * args.steps / tg / 1e6, 1), "unit": "MLUPS",
+                              "hbm_frac_of_measured": round(BYTES_PER_NODE["fp32_g16"] * N / (tg / args.steps) / 1e9 / peak, 4)}
+        dg.close()
+        extras["error_vs_oracle"] = accuracy_check()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    line = {
+        "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "droplet evaporation, open outflow, Dirichlet 0.95Tc edges, "
+                               "R=640, 4096x4096, FP32 fused step",
+                   "nx": NX, "ny": NY, "l2": "inputs larger than L2 (2 GiB state)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "tile": list(dom.tile())},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+        "gpu_launches": args.steps,
+        **extras,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dom.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on the host cores, on a bounded
+    sample of the same workload; rank 0 only."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    c = make_case(512)
+    s = oracle.Sim(c.nx, c.ny, c.params, c.bc)
+    s.init(*c.fields())
+    for _ in range(min(args.warmup, 3)):
+        s.step(1)
+    steps = args.steps
+    per = max(1, min(8, 200 // max(steps, 1)))   # keep the whole run to a few minutes
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.step(per)
+    dt = time.perf_counter() - t0
+    mlups = c.nx * c.ny * per * steps / dt / 1e6
+    sample = "%dx%d sample of the 4096x4096 setup, %d x %d FP64 steps" % (c.nx, c.ny, steps, per)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
+        "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "droplet evaporation, open outflow, Dirichlet 0.95Tc edges, "
+                               "R=640, 4096x4096, FP32 fused step", "nx": NX, "ny": NY},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * C ABI of the GB300 (sm_103a) implementation of the coupled time step of the
+ * thermal lattice Boltzmann model for liquid-vapor phase change of Wang, Huang
+ * & He (arXiv 2205.00686): a D2Q9 multiple-relaxation-time pseudopotential
+ * flow lattice (Section 2) coupled to the paper's D2Q5 multiple-relaxation-
+ * time temperature lattice with the rho c_v-weighted streaming (Section 3.2,
+ * Eq. 39), with the wetting, Dirichlet, open, periodic and no-slip boundaries
+ * of Sections 3.3 and 4.
+ *
+ * Conventions shared by every entry point:
+ *  - Fields on the host are row-major double arrays [ny][nx], x fastest, node
+ *    (0,0) at the south-west corner; gravity points to -y.
+ *  - Populations on the host are double arrays [q][ny][nx] (q = 9 for f, the
+ *    D2Q9 order of Eq. 2; q = 5 for g, the D2Q5 order of Eq. 26).
+ *  - The caller owns every host array; the library copies what it needs and
+ *    keeps no host pointer.  The library owns the device memory it allocates.
+ *  - Work is queued on the context's CUDA stream; entry points that return
+ *    host data synchronise that stream.
+ *  - Every function returns LBM_OK (0) or a negative LBM_E* code and never
+ *    throws.  A device-side error (negative psi^2, non-finite state) is sticky:
+ *    it is reported by the next synchronising call and clears only on
+ *    lbm_init_fields, lbm_set_populations or lbm_load.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)      /* bad argument, size or boundary combination     */
+#define LBM_ENOMEM (-2)      /* device or host allocation failed               */
+#define LBM_ENONFINITE (-3)  /* a NaN / Inf appeared in rho or T               */
+#define LBM_EPSI (-4)        /* psi^2 = 2 (rho c_s^2 - p_EOS) < 0 at some node  */
+#define LBM_ECUDA (-5)       /* a CUDA runtime call failed                     */
+#define LBM_EIO (-6)         /* checkpoint file could not be read or written  */
+#define LBM_ESTATE (-7)      /* call out of order (e.g. step before init)     */
+
+/* ---- precision of storage and arithmetic ------------------------------- */
+typedef enum {
+    LBM_FP64 = 0,      /* f, g, P stored and computed in double             */
+    LBM_FP32 = 1,      /* f, g, P stored and computed in float              */
+    LBM_FP32_G16 = 2   /* as LBM_FP32, but g stored in IEEE half             */
+} lbm_prec;
+
+/* ---- boundaries ---------------------------------------------------------- */
+enum { LBM_EDGE_W = 0, LBM_EDGE_E = 1, LBM_EDGE_S = 2, LBM_EDGE_N = 3 };
+typedef enum { LBM_PERIODIC = 0, LBM_WALL = 1, LBM_OPEN = 2 } lbm_flow_bc;
+typedef enum { LBM_T_PERIODIC = 0, LBM_T_DIRICHLET = 1, LBM_T_ADIABATIC = 2 } lbm_therm_bc;
+
+/* Boundary specification (Sections 3.3 and 4).
+ *  flow[e]:  LBM_PERIODIC, LBM_WALL (halfway bounce-back no-slip wall with the
+ *            Ding-Spelt wetting ghost layer; south/north edges only) or
+ *            LBM_OPEN (zero-gradient extrapolation of the unknown populations).
+ *  therm[e]: LBM_T_PERIODIC, LBM_T_DIRICHLET (halfway anti-bounce-back to
+ *            T_edge[e]) or LBM_T_ADIABATIC (halfway bounce-back).
+ *  An axis is periodic for both lattices on both of its edges or not at all.
+ *  theta_deg: equilibrium contact angle of walls (Section 3.3).
+ *  heater_x0..heater_x1-1: south-edge nodes held at T_heater instead of
+ *  T_edge[S] (Section 4.3). */
+typedef struct {
+    int flow[4];
+    int therm[4];
+    double T_edge[4];
+    double theta_deg;
+    int heater_x0, heater_x1;
+    double T_heater;
+} lbm_bc;
+
+/* ---- physical and numerical parameters (all double) -------------------- *
+ * a, b, R, omega: Peng-Robinson EOS (Section 2, Eq. 10), T_c = 0.0778 a /
+ *   (0.45724 b R).
+ * G, sigma: interaction strength of Eq. 9 and the tunable sigma of Eq. 8.
+ * nu: kinematic viscosity, s_p = 1/(3 nu + 1/2).  s0, s_e, s_eps, s_j, s_q: the
+ *   other diagonal entries of S (Section 2).
+ * lambda: thermal conductivity; varsigma_1 = varsigma_2 = 1/(lambda/c_s^2 +
+ *   1/2) with c_s^2 = w_dot/2 (Section 3.2.2).  cv: specific heat.  w_dot: the
+ *   D2Q5 rest-weight parameter (w_0 = 1 - w_dot, w_1..4 = w_dot/4).  vs0, vs3,
+ *   vs4: the other entries of Lambda.
+ * gravity: g of the body force (rho - rho_ave)(0, -g) (Section 4.3).
+ * rho_ref, T_ref: storage references; populations are stored as deviations
+ *   f_i - w_i rho_ref and g_i - w^_i T_ref.  rho_ref <= 0 means "the mean of
+ *   the initial density"; T_ref <= 0 means "the mean of the initial T".
+ * frozen_flow (test hook): u = 0 and rho fixed; only g advances.
+ * frozen_thermal (isothermal hook): g fixed; only f advances. */
+typedef struct {
+    double a, b, R, omega;
+    double G, sigma;
+    double nu, s0, s_e, s_eps, s_j, s_q;
+    double lambda, cv, w_dot, vs0, vs3, vs4;
+    double gravity;
+    double rho_ref, T_ref;
+    int frozen_flow, frozen_thermal;
+} lbm_params;
+
+/* Diagnostics (Sections 3.3 and 4), accumulated in double on the device:
+ * mass = sum rho, energy = sum rho c_v T, liquid_* over nodes with rho above
+ * the interface level (rho_l + rho_g)/2, liquid_area_smooth = sum of
+ * clamp((rho - rho_g)/(rho_l - rho_g), 0, 1), diameters of the equivalent
+ * disc (or half disc when sessile), max_u = max |u|. */
+typedef struct {
+    double mass, energy, liquid_mass, liquid_area, liquid_area_smooth;
+    double diameter, diameter_smooth, max_u;
+    long long step;
+    int nonfinite;
+} lbm_diag;
+
+typedef struct lbm_ctx lbm_ctx;
+typedef struct lbm_batch lbm_batch;
+
+/* Fills *p with the paper's constants and the library's readings:
+ * a = 3/49, b = 2/21, R = 1, omega = 0.344, G = -1, sigma = 1.25, nu = 0.1,
+ * cv = 5, lambda = 1/3, w_dot = 2/3, every other rate 1.0, gravity 0. */
+int lbm_default_params(lbm_params* p);
+
+/* Device bytes lbm_create needs for an nx x ny domain at precision prec
+ * (both ping-pong copies of f, g and P).  Returns 0 for invalid sizes. */
+size_t lbm_state_bytes(int nx, int ny, int prec);
+
+/* Creates a simulation context.
+ *  stream: a cudaStream_t (as void*) to queue work on, or NULL for a stream
+ *          the library creates and owns.  The legacy default stream cannot be
+ *          captured into CUDA graphs; pass a created stream.
+ *  device_mem / device_bytes: optional caller-owned device buffer of at least
+ *          lbm_state_bytes(nx, ny, prec) bytes, 256-byte aligned, to hold the
+ *          state (e.g. from a PyTorch allocation); NULL to let the library
+ *          allocate.  The caller keeps it alive until lbm_destroy.
+ * Errors: LBM_EINVAL (sizes < 1, bad precision, unsupported boundary
+ * combination, non-positive cv / nu / lambda, w_dot outside (0,1)),
+ * LBM_ENOMEM, LBM_ECUDA.  *out is NULL on failure. */
+int lbm_create(int nx, int ny, const lbm_params* params, const lbm_bc* bc, int prec,
+               void* stream, void* device_mem, size_t device_bytes, lbm_ctx** out);
+
+/* Sets the state at t = 0 from host fields (each [ny][nx], double):
+ * f = f^eq(rho, u) of Eq. 3, g = w^ T (Eq. 22), P history cleared; the first
+ * step then takes d_t^2 T = 0.  Clears the sticky error.  Synchronises. */
+int lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                    const double* T);
+
+/* Queues n coupled time steps (n >= 0), asynchronous on the context stream.
+ * Returns LBM_ESTATE before initialisation, LBM_ECUDA on launch failure; a
+ * sticky device error from an earlier step is returned without queuing. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Copies rho, u = (sum c f + F/2)/rho (Eq. 11) and T of the current state to
+ * host arrays [ny][nx]; any pointer may be NULL.  Synchronises and returns
+ * the sticky device error if one is set. */
+int lbm_get_rho_u_T(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* T);
+
+/* Diagnostics of the current state; rho_l and rho_g set the interface level
+ * and the smooth liquid fraction; sessile selects the half-disc diameter.
+ * Synchronises. */
+int lbm_diagnostics(lbm_ctx* ctx, double rho_l, double rho_g, int sessile, lbm_diag* out);
+
+/* Populations of the current state as absolute values (not deviations):
+ * f [9][ny][nx], g [5][ny][nx], P [ny][nx] (P = Q/(rho c_v) of the last
+ * step); any pointer may be NULL.  Synchronises. */
+int lbm_get_populations(lbm_ctx* ctx, double* f, double* g, double* P);
+
+/* Replaces the state by host populations (same layout, absolute values),
+ * sets the step counter to `step` (step 0 takes d_t^2 T = 0 on its first
+ * step) and the mean density of the previous step used by the buoyancy
+ * force to rho_ave_prev.  Clears the sticky error.  Synchronises. */
+int lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g, const double* P,
+                        long long step, double rho_ave_prev);
+
+/* Number of completed steps. */
+long long lbm_step_count(const lbm_ctx* ctx);
+
+/* Waits for queued work; returns the sticky device error, if any. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Checkpoint: a raw binary of the current-state device buffers, the step
+ * counter, the buoyancy mass history, params and bc, with a header and a
+ * CRC-32.  lbm_load requires a context of the same nx, ny and precision and
+ * restores it bit for bit.  Both synchronise.  LBM_EIO on file errors or a
+ * CRC / header mismatch. */
+int lbm_save(lbm_ctx* ctx, const char* path);
+int lbm_load(lbm_ctx* ctx, const char* path);
+
+/* Frees the context (synchronising first).  NULL is accepted. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Human-readable text of the last error seen by this context (never NULL). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* ---- batched stepping of independent domains --------------------------- *
+ * A batch advances every attached context by one coupled step per launch of
+ * one persistent kernel that walks a shared work list of (domain, tile)
+ * units, so hundreds of domains of uneven size share the GPU.  Attached
+ * contexts must have the same precision and the same physical parameters
+ * (everything in lbm_params except rho_ref / T_ref); sizes, boundaries and
+ * edge temperatures may differ.  Each context's own stream is not used while
+ * it is attached: the batch's stream is. */
+
+/* stream: as in lbm_create. */
+int lbm_batch_create(void* stream, lbm_batch** out);
+/* Adds / removes a context (synchronising the batch stream first).  A
+ * context belongs to at most one batch. LBM_EINVAL on precision or
+ * parameter mismatch. */
+int lbm_batch_attach(lbm_batch* b, lbm_ctx* ctx);
+int lbm_batch_detach(lbm_batch* b, lbm_ctx* ctx);
+/* Number of attached contexts. */
+int lbm_batch_size(const lbm_batch* b);
+/* Queues n steps of every attached context on the batch stream. */
+int lbm_batch_step(lbm_batch* b, int n);
+/* Waits for the batch stream; returns the first sticky device error among
+ * the attached contexts (and records it in that context). */
+int lbm_batch_sync(lbm_batch* b);
+void lbm_batch_destroy(lbm_batch* b);
+
+/* ---- launch configuration ------------------------------------------------ *
+ * Tile of the fused step: a strip of (threads - 8) columns swept over a
+ * segment of `rows` rows.  threads is 128 or 256; rows >= 1.  The autotuner
+ * times the candidates on a scratch domain of the same size and precision
+ * and applies the fastest; its choice is cached per (precision, size). */
+int lbm_set_tile(lbm_ctx* ctx, int threads, int rows);
+int lbm_get_tile(const lbm_ctx* ctx, int* threads, int* rows);
+int lbm_autotune(lbm_ctx* ctx, int steps_per_trial);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_H */

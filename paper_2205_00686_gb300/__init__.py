@@ -1,0 +1,301 @@
+"""GB300 (sm_103a) coupled thermal lattice Boltzmann step for liquid-vapor
+phase change (Wang, Huang & He, arXiv 2205.00686).
+
+Thin Python binding of the C ABI in ``include/lbm.h``: the functions keep the
+ABI's names and only marshal arguments; every step of the method runs in the
+CUDA library ``liblbm_gb300.so`` built from ``csrc/``.  There is no CPU
+fallback: if the library is missing or cannot load, every call raises.
+
+Host arrays are float64 ``[ny][nx]`` fields or ``[q][ny][nx]`` populations,
+as numpy arrays or CPU torch tensors (pinned tensors make the copies
+asynchronous-capable DMA).  Streams are passed as raw ``cudaStream_t``
+handles, e.g. ``torch.cuda.Stream().cuda_stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ENONFINITE, LBM_EPSI, LBM_ECUDA, LBM_EIO, LBM_ESTATE = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+LBM_FP64, LBM_FP32, LBM_FP32_G16 = 0, 1, 2
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp32_g16": LBM_FP32_G16}
+LBM_PERIODIC, LBM_WALL, LBM_OPEN = 0, 1, 2
+LBM_T_PERIODIC, LBM_T_DIRICHLET, LBM_T_ADIABATIC = 0, 1, 2
+
+# every symbol include/lbm.h declares
+ABI_FUNCTIONS = (
+    "lbm_default_params", "lbm_state_bytes", "lbm_create", "lbm_init_fields", "lbm_step",
+    "lbm_get_rho_u_T", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
+    "lbm_step_count", "lbm_sync", "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
+    "lbm_batch_create", "lbm_batch_attach", "lbm_batch_detach", "lbm_batch_size",
+    "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy", "lbm_set_tile", "lbm_get_tile",
+    "lbm_autotune",
+)
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        super().__init__("lbm error %d%s" % (code, (": " + msg) if msg else ""))
+        self.code = code
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "a", "b", "R", "omega", "G", "sigma", "nu", "s0", "s_e", "s_eps", "s_j", "s_q",
+        "lambda_", "cv", "w_dot", "vs0", "vs3", "vs4", "gravity", "rho_ref", "T_ref")] + [
+        ("frozen_flow", ctypes.c_int), ("frozen_thermal", ctypes.c_int)]
+
+
+class lbm_bc(ctypes.Structure):
+    _fields_ = [("flow", ctypes.c_int * 4), ("therm", ctypes.c_int * 4),
+                ("T_edge", ctypes.c_double * 4), ("theta_deg", ctypes.c_double),
+                ("heater_x0", ctypes.c_int), ("heater_x1", ctypes.c_int),
+                ("T_heater", ctypes.c_double)]
+
+
+class lbm_diag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "mass", "energy", "liquid_mass", "liquid_area", "liquid_area_smooth",
+        "diameter", "diameter_smooth", "max_u")] + [
+        ("step", ctypes.c_longlong), ("nonfinite", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    """The loaded CUDA library (raises if it is missing or cannot load)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("CUDA library %s is missing; run __graft_entry__.build() or "
+                              "python -m paper_2205_00686_gb300._build" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, B, D = ctypes.POINTER(lbm_params), ctypes.POINTER(lbm_bc), ctypes.POINTER(lbm_diag)
+        sig = {
+            "lbm_default_params": ([P], ctypes.c_int),
+            "lbm_state_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+            "lbm_create": ([ctypes.c_int, ctypes.c_int, P, B, ctypes.c_int, _vp, _vp,
+                            ctypes.c_size_t, ctypes.POINTER(_vp)], ctypes.c_int),
+            "lbm_init_fields": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+            "lbm_step": ([_vp, ctypes.c_int], ctypes.c_int),
+            "lbm_get_rho_u_T": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+            "lbm_diagnostics": ([_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, D],
+                                ctypes.c_int),
+            "lbm_get_populations": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+            "lbm_set_populations": ([_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_double],
+                                    ctypes.c_int),
+            "lbm_step_count": ([_vp], ctypes.c_longlong),
+            "lbm_sync": ([_vp], ctypes.c_int),
+            "lbm_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+            "lbm_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
+            "lbm_destroy": ([_vp], None),
+            "lbm_last_error": ([_vp], ctypes.c_char_p),
+            "lbm_batch_create": ([_vp, ctypes.POINTER(_vp)], ctypes.c_int),
+            "lbm_batch_attach": ([_vp, _vp], ctypes.c_int),
+            "lbm_batch_detach": ([_vp, _vp], ctypes.c_int),
+            "lbm_batch_size": ([_vp], ctypes.c_int),
+            "lbm_batch_step": ([_vp, ctypes.c_int], ctypes.c_int),
+            "lbm_batch_sync": ([_vp], ctypes.c_int),
+            "lbm_batch_destroy": ([_vp], None),
+            "lbm_set_tile": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "lbm_get_tile": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                             ctypes.c_int),
+            "lbm_autotune": ([_vp, ctypes.c_int], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Address of a host float64 array (numpy or CPU torch tensor), or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("expected a C-contiguous float64 array")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.is_cuda:
+            raise TypeError("expected a contiguous float64 CPU tensor")
+        return a.data_ptr()
+    raise TypeError("unsupported array type %r" % type(a))
+
+
+def make_params(d: dict) -> lbm_params:
+    p = lbm_params()
+    lib().lbm_default_params(ctypes.byref(p))
+    for k, v in d.items():
+        name = "lambda_" if k == "lambda" else k
+        if any(name == f[0] for f in lbm_params._fields_):
+            setattr(p, name, v)
+    return p
+
+
+def make_bc(d: dict) -> lbm_bc:
+    b = lbm_bc()
+    for e in range(4):
+        b.flow[e] = int(d["flow"][e])
+        b.therm[e] = int(d["therm"][e])
+        b.T_edge[e] = float(d.get("T_edge", (0.0,) * 4)[e])
+    b.theta_deg = float(d.get("theta_deg", 90.0))
+    b.heater_x0 = int(d.get("heater_x0", 0))
+    b.heater_x1 = int(d.get("heater_x1", 0))
+    b.T_heater = float(d.get("T_heater", 0.0))
+    return b
+
+
+def _check(rc, ctx=None):
+    if rc != LBM_OK:
+        msg = lib().lbm_last_error(ctx).decode() if ctx else ""
+        raise LbmError(rc, msg)
+    return rc
+
+
+def lbm_state_bytes(nx: int, ny: int, prec) -> int:
+    return int(lib().lbm_state_bytes(nx, ny, PRECISIONS.get(prec, prec)))
+
+
+class Domain:
+    """One simulation context (``lbm_ctx``)."""
+
+    def __init__(self, nx: int, ny: int, params: dict, bc: dict, prec="fp32", stream=None,
+                 device_mem=None, device_bytes=0):
+        self.nx, self.ny = int(nx), int(ny)
+        self.prec = PRECISIONS.get(prec, prec)
+        self._p = make_params(params)
+        self._b = make_bc(bc)
+        h = _vp()
+        _check(lib().lbm_create(self.nx, self.ny, ctypes.byref(self._p), ctypes.byref(self._b),
+                                self.prec, stream, device_mem, int(device_bytes),
+                                ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f(self, a):
+        return a if a is None or hasattr(a, "data_ptr") else np.ascontiguousarray(a, np.float64)
+
+    def init_fields(self, rho, ux, uy, T):
+        arrs = [self._f(a) for a in (rho, ux, uy, T)]
+        _check(lib().lbm_init_fields(self._h, *[_ptr(a) for a in arrs]), self._h)
+
+    def step(self, n: int = 1):
+        _check(lib().lbm_step(self._h, int(n)), self._h)
+
+    def sync(self):
+        return _check(lib().lbm_sync(self._h), self._h)
+
+    def get_rho_u_T(self, out=None):
+        out = out or tuple(np.empty((self.ny, self.nx)) for _ in range(4))
+        _check(lib().lbm_get_rho_u_T(self._h, *[_ptr(a) for a in out]), self._h)
+        return out
+
+    def diagnostics(self, rho_l, rho_g, sessile=False) -> dict:
+        d = lbm_diag()
+        _check(lib().lbm_diagnostics(self._h, rho_l, rho_g, int(sessile), ctypes.byref(d)),
+               self._h)
+        return {k: getattr(d, k) for k, _ in lbm_diag._fields_}
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        g = np.empty((5, self.ny, self.nx))
+        P = np.empty((self.ny, self.nx))
+        _check(lib().lbm_get_populations(self._h, _ptr(f), _ptr(g), _ptr(P)), self._h)
+        return f, g, P
+
+    def set_populations(self, f, g, P, step: int, rho_ave_prev: float):
+        f, g, P = (np.ascontiguousarray(a, np.float64) for a in (f, g, P))
+        _check(lib().lbm_set_populations(self._h, _ptr(f), _ptr(g), _ptr(P), int(step),
+                                         float(rho_ave_prev)), self._h)
+
+    @property
+    def step_count(self) -> int:
+        return int(lib().lbm_step_count(self._h))
+
+    def save(self, path: str):
+        _check(lib().lbm_save(self._h, path.encode()), self._h)
+
+    def load(self, path: str):
+        _check(lib().lbm_load(self._h, path.encode()), self._h)
+
+    def set_tile(self, threads: int, rows: int):
+        _check(lib().lbm_set_tile(self._h, threads, rows), self._h)
+
+    def tile(self):
+        t, r = ctypes.c_int(), ctypes.c_int()
+        lib().lbm_get_tile(self._h, ctypes.byref(t), ctypes.byref(r))
+        return t.value, r.value
+
+    def autotune(self, steps_per_trial: int = 10):
+        _check(lib().lbm_autotune(self._h, steps_per_trial), self._h)
+        return self.tile()
+
+    @property
+    def last_error(self) -> str:
+        return lib().lbm_last_error(self._h).decode()
+
+
+class Batch:
+    """Batched stepping of many domains (``lbm_batch``)."""
+
+    def __init__(self, stream=None):
+        h = _vp()
+        _check(lib().lbm_batch_create(stream, ctypes.byref(h)))
+        self._h = h
+        self.members = []
+
+    def attach(self, d: Domain):
+        _check(lib().lbm_batch_attach(self._h, d.handle), d.handle)
+        self.members.append(d)
+
+    def detach(self, d: Domain):
+        _check(lib().lbm_batch_detach(self._h, d.handle), d.handle)
+        self.members.remove(d)
+
+    def __len__(self):
+        return int(lib().lbm_batch_size(self._h))
+
+    def step(self, n: int = 1):
+        _check(lib().lbm_batch_step(self._h, int(n)))
+
+    def sync(self):
+        return lib().lbm_batch_sync(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_batch_destroy(self._h)
+            self._h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,926 @@
+// C ABI of the library (declared in include/lbm.h): simulation contexts,
+// device memory layout, work-unit lists, CUDA-graph replay of the fused step,
+// batched stepping of many domains, the tile autotuner and checkpoints.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+namespace {
+
+const int kGraphLen = 32;      // launches per captured graph
+const size_t kAlign = 256;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    int pitch;
+    size_t planeF, planeG, planeP, total;
+};
+
+// Planes are [ny][pitch] with pitch a multiple of 64 elements, so every plane
+// (and every row) starts on a 128-byte boundary; the kernels address plane q
+// at q * ny * pitch elements, so planes are packed without extra padding.
+Layout layout_for(int nx, int ny, int prec) {
+    Layout L;
+    L.pitch = (int)round_up((size_t)nx, 64);
+    L.planeF = (size_t)L.pitch * ny * elem_f(prec);
+    L.planeG = (size_t)L.pitch * ny * elem_g(prec);
+    L.planeP = (size_t)L.pitch * ny * elem_P(prec);
+    L.total = 2 * (9 * L.planeF + 5 * L.planeG + L.planeP);
+    return L;
+}
+
+bool bc_valid(int nx, int ny, const lbm_bc* bc) {
+    for (int e = 0; e < 4; ++e) {
+        if (bc->flow[e] < 0 || bc->flow[e] > 2 || bc->therm[e] < 0 || bc->therm[e] > 2) return false;
+        if ((bc->flow[e] == LBM_PERIODIC) != (bc->therm[e] == LBM_T_PERIODIC)) return false;
+    }
+    if ((bc->flow[LBM_EDGE_W] == LBM_PERIODIC) != (bc->flow[LBM_EDGE_E] == LBM_PERIODIC)) return false;
+    if ((bc->flow[LBM_EDGE_S] == LBM_PERIODIC) != (bc->flow[LBM_EDGE_N] == LBM_PERIODIC)) return false;
+    if (bc->flow[LBM_EDGE_W] == LBM_WALL || bc->flow[LBM_EDGE_E] == LBM_WALL) return false;
+    if (bc->flow[LBM_EDGE_W] != LBM_PERIODIC && nx < 2) return false;
+    if (bc->flow[LBM_EDGE_S] != LBM_PERIODIC && ny < 2) return false;
+    return true;
+}
+
+PhysD phys_from(const lbm_params* p) {
+    PhysD d;
+    d.a = p->a;
+    d.b = p->b;
+    d.Rg = p->R;
+    d.omega = p->omega;
+    d.G = p->G;
+    d.sigma = p->sigma;
+    d.s_e = p->s_e;
+    d.s_eps = p->s_eps;
+    d.s_q = p->s_q;
+    d.s_p = 1.0 / (3.0 * p->nu + 0.5);                       // nu = c_s^2 (1/s_p - 1/2)
+    d.cv = p->cv;
+    d.w_dot = p->w_dot;
+    d.vs1 = 1.0 / (p->lambda / (0.5 * p->w_dot) + 0.5);      // lambda = (1/vs - 1/2) w_dot/2
+    d.vs3 = p->vs3;
+    d.vs4 = p->vs4;
+    d.gravity = p->gravity;
+    d.frozen_flow = p->frozen_flow;
+    d.frozen_thermal = p->frozen_thermal;
+    return d;
+}
+
+bool same_physics(const lbm_params& a, const lbm_params& b) {
+    lbm_params x = a, y = b;
+    x.rho_ref = y.rho_ref = 0.0;
+    x.T_ref = y.T_ref = 0.0;
+    return memcmp(&x, &y, sizeof(x)) == 0;
+}
+
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
+    static uint32_t table[256];
+    static bool init = false;
+    if (!init) {
+        for (uint32_t i = 0; i < 256; ++i) {
+            uint32_t c = i;
+            for (int k = 0; k < 8; ++k) c = (c & 1) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+            table[i] = c;
+        }
+        init = true;
+    }
+    const unsigned char* p = (const unsigned char*)data;
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFF] ^ (crc >> 8);
+    return ~crc;
+}
+
+// tile autotuner cache: (prec, nx, ny) -> (threads, rows)
+std::map<std::tuple<int, int, int>, std::pair<int, int>>& tune_cache() {
+    static std::map<std::tuple<int, int, int>, std::pair<int, int>> m;
+    return m;
+}
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+void build_units(const Inst& I, int inst_index, int threads, int rows, std::vector<Unit>& out) {
+    const int W = threads - 8;
+    for (int y0 = 0; y0 < I.ny; y0 += rows)
+        for (int x0 = 0; x0 < I.nx; x0 += W) {
+            Unit u;
+            u.inst = inst_index;
+            u.x0 = x0;
+            u.x1 = std::min(I.nx, x0 + W);
+            u.y0 = y0;
+            u.y1 = std::min(I.ny, y0 + rows);
+            out.push_back(u);
+        }
+}
+
+// default segment height: enough units to fill the GPU twice, 16..256 rows
+int default_rows(int prec, int threads, int nx, int ny) {
+    int ctas = 1;
+    size_t smem = 0;
+    step_occupancy(prec, threads, &ctas, &smem);
+    const long long slots = (long long)std::max(ctas, 1) * num_sms();
+    const int strips = (nx + threads - 9) / (threads - 8);
+    int rows = 256;
+    while (rows > 16 && (long long)strips * ((ny + rows - 1) / rows) < 2 * slots) rows /= 2;
+    return std::max(1, std::min(rows, ny));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+struct lbm_ctx {
+    int nx = 0, ny = 0, prec = 0;
+    lbm_params params;
+    lbm_bc bc;
+    PhysD phys;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* mem = nullptr;
+    bool own_mem = false;
+    Layout lay;
+    Inst inst;                 // host copy (pointers into mem)
+    void* small = nullptr;     // Ctl | Inst | sched
+    Ctl* ctl = nullptr;
+    Inst* inst_dev = nullptr;
+    unsigned* sched = nullptr;
+    Unit* units = nullptr;
+    int n_units = 0, grid = 1, threads = 128, rows = 64;
+    cudaGraphExec_t graph = nullptr;
+    long long step = 0;
+    bool initialized = false;
+    int sticky = LBM_OK;
+    std::string err;
+    double* fields = nullptr;  // 4 N doubles, lazily allocated
+    void* diag_scratch = nullptr;
+    double* diag_out = nullptr;
+    lbm_batch* batch = nullptr;
+};
+
+struct lbm_batch {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<lbm_ctx*> members;
+    Inst* insts = nullptr;
+    Unit* units = nullptr;
+    unsigned* sched = nullptr;
+    int n_units = 0, grid = 1, threads = 128, rows = 64, prec = -1;
+    PhysD phys;
+    lbm_params params;
+    cudaGraphExec_t graph = nullptr;
+};
+
+static int set_err(lbm_ctx* c, int code, const char* msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+static int cuda_err(lbm_ctx* c, cudaError_t e, const char* where) {
+    if (e == cudaSuccess) return LBM_OK;
+    if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+}
+
+static int map_device_err(int bits) {
+    if (bits & ERR_PSI) return LBM_EPSI;
+    if (bits & ERR_NONFINITE) return LBM_ENONFINITE;
+    return LBM_OK;
+}
+
+static void drop_graph(cudaGraphExec_t* g) {
+    if (*g) cudaGraphExecDestroy(*g);
+    *g = nullptr;
+}
+
+// (re)builds the unit list and persistent grid of a context for its tile
+static int ctx_apply_tile(lbm_ctx* c, int threads, int rows) {
+    std::vector<Unit> us;
+    build_units(c->inst, 0, threads, rows, us);
+    int ctas = 1;
+    size_t smem = 0;
+    if (step_occupancy(c->prec, threads, &ctas, &smem)) return set_err(c, LBM_ECUDA, "occupancy query failed");
+    if (ctas < 1) return set_err(c, LBM_EINVAL, "tile does not fit on an SM");
+    cudaStreamSynchronize(c->stream);
+    if (c->units) cudaFree(c->units);
+    c->units = nullptr;
+    cudaError_t e = cudaMalloc(&c->units, us.size() * sizeof(Unit));
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc(units)");
+    e = cudaMemcpy(c->units, us.data(), us.size() * sizeof(Unit), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaMemcpy(units)");
+    c->n_units = (int)us.size();
+    c->grid = (int)std::min<long long>((long long)c->n_units, (long long)ctas * num_sms());
+    c->threads = threads;
+    c->rows = rows;
+    drop_graph(&c->graph);
+    return LBM_OK;
+}
+
+static StepLaunch ctx_launch(const lbm_ctx* c) {
+    StepLaunch L;
+    L.insts = c->inst_dev;
+    L.units = c->units;
+    L.n_units = c->n_units;
+    L.n_inst = 1;
+    L.sched = c->sched;
+    L.grid = c->grid;
+    L.phys = c->phys;
+    return L;
+}
+
+static int enqueue_steps(cudaStream_t st, cudaGraphExec_t* graph, const StepLaunch& L, int prec,
+                         int threads, int n, lbm_ctx* errctx) {
+    if (n >= kGraphLen) {
+        if (!*graph) {
+            cudaGraph_t g;
+            cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_err(errctx, e, "cudaStreamBeginCapture");
+            for (int i = 0; i < kGraphLen; ++i) step_launch(prec, threads, L, st);
+            e = cudaStreamEndCapture(st, &g);
+            if (e != cudaSuccess) return cuda_err(errctx, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                *graph = nullptr;
+                return cuda_err(errctx, e, "cudaGraphInstantiate");
+            }
+        }
+        for (int i = 0; i < n / kGraphLen; ++i) {
+            cudaError_t e = cudaGraphLaunch(*graph, st);
+            if (e != cudaSuccess) return cuda_err(errctx, e, "cudaGraphLaunch");
+        }
+        n %= kGraphLen;
+    }
+    for (int i = 0; i < n; ++i)
+        if (step_launch(prec, threads, L, st)) return cuda_err(errctx, cudaGetLastError(), "step launch");
+    return LBM_OK;
+}
+
+static int ctx_read_ctl(lbm_ctx* c, Ctl* out) {
+    cudaError_t e = cudaMemcpyAsync(out, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_err(c, e, "reading the control block");
+}
+
+static int ctx_check(lbm_ctx* c) {
+    Ctl h;
+    int rc = ctx_read_ctl(c, &h);
+    if (rc) return rc;
+    if (h.err && c->sticky == LBM_OK) {
+        c->sticky = map_device_err(h.err);
+        c->err = c->sticky == LBM_EPSI ? "psi^2 < 0 at some node (density above the EOS range)"
+                                       : "non-finite density or temperature";
+    }
+    return c->sticky;
+}
+
+static int ensure_fields(lbm_ctx* c) {
+    if (c->fields) return LBM_OK;
+    const size_t N = (size_t)c->nx * c->ny;
+    cudaError_t e = cudaMalloc(&c->fields, 4 * N * sizeof(double));
+    if (e != cudaSuccess) {
+        c->fields = nullptr;
+        return cuda_err(c, e, "cudaMalloc(fields)");
+    }
+    e = cudaMalloc(&c->diag_scratch, diag_scratch_bytes((long long)N));
+    if (e == cudaSuccess) e = cudaMemset(c->diag_scratch, 0, diag_scratch_bytes((long long)N));
+    if (e == cudaSuccess) e = cudaMalloc(&c->diag_out, 16 * sizeof(double));
+    return cuda_err(c, e, "cudaMalloc(diagnostics)");
+}
+
+extern "C" {
+
+int lbm_default_params(lbm_params* p) {
+    if (!p) return LBM_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->a = 3.0 / 49.0;
+    p->b = 2.0 / 21.0;
+    p->R = 1.0;
+    p->omega = 0.344;
+    p->G = -1.0;
+    p->sigma = 1.25;
+    p->nu = 0.1;
+    p->s0 = p->s_e = p->s_eps = p->s_j = p->s_q = 1.0;
+    p->lambda = 1.0 / 3.0;
+    p->cv = 5.0;
+    p->w_dot = 2.0 / 3.0;
+    p->vs0 = p->vs3 = p->vs4 = 1.0;
+    return LBM_OK;
+}
+
+size_t lbm_state_bytes(int nx, int ny, int prec) {
+    if (nx < 1 || ny < 1 || prec < 0 || prec > 2) return 0;
+    return layout_for(nx, ny, prec).total;
+}
+
+int lbm_create(int nx, int ny, const lbm_params* params, const lbm_bc* bc, int prec,
+               void* stream, void* device_mem, size_t device_bytes, lbm_ctx** out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || !params || !bc || prec < 0 || prec > 2) return LBM_EINVAL;
+    if (nx > (1 << 20) || ny > (1 << 20)) return LBM_EINVAL;
+    if (!bc_valid(nx, ny, bc)) return LBM_EINVAL;
+    if (!(params->cv > 0) || !(params->nu > 0) || !(params->lambda > 0) ||
+        !(params->w_dot > 0 && params->w_dot < 1) || params->G == 0.0 || !(params->b > 0) ||
+        !(params->s_e > 0 && params->s_e < 2) || !(params->s_eps > 0 && params->s_eps < 2))
+        return LBM_EINVAL;
+    if (device_mem && ((uintptr_t)device_mem % kAlign || device_bytes < lbm_state_bytes(nx, ny, prec)))
+        return LBM_EINVAL;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ENOMEM;
+    c->nx = nx;
+    c->ny = ny;
+    c->prec = prec;
+    c->params = *params;
+    c->bc = *bc;
+    c->phys = phys_from(params);
+    c->lay = layout_for(nx, ny, prec);
+    cudaError_t e = cudaSuccess;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        c->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) {
+        if (device_mem) {
+            c->mem = device_mem;
+        } else {
+            e = cudaMalloc(&c->mem, c->lay.total);
+            c->own_mem = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&c->small, round_up(sizeof(Ctl), kAlign) + round_up(sizeof(Inst), kAlign) + kAlign);
+    if (e != cudaSuccess) {
+        int rc = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+        lbm_destroy(c);
+        return rc;
+    }
+    char* sp = (char*)c->small;
+    c->ctl = (Ctl*)sp;
+    c->inst_dev = (Inst*)(sp + round_up(sizeof(Ctl), kAlign));
+    c->sched = (unsigned*)(sp + round_up(sizeof(Ctl), kAlign) + round_up(sizeof(Inst), kAlign));
+    char* m = (char*)c->mem;
+    Inst& I = c->inst;
+    memset(&I, 0, sizeof(I));
+    for (int p = 0; p < 2; ++p) {
+        I.f[p] = m + p * 9 * c->lay.planeF;
+        I.g[p] = m + 18 * c->lay.planeF + p * 5 * c->lay.planeG;
+        I.P[p] = m + 18 * c->lay.planeF + 10 * c->lay.planeG + p * c->lay.planeP;
+    }
+    I.ctl = c->ctl;
+    I.nx = nx;
+    I.ny = ny;
+    // the plane stride used by the kernels is ny * pitch elements: keep the
+    // rounded plane sizes consistent with it
+    I.pitch = c->lay.pitch;
+    for (int k = 0; k < 4; ++k) {
+        I.flow[k] = bc->flow[k];
+        I.therm[k] = bc->therm[k];
+        I.T_edge[k] = bc->T_edge[k];
+    }
+    I.heater_x0 = bc->heater_x0;
+    I.heater_x1 = bc->heater_x1;
+    I.T_heater = bc->T_heater;
+    I.cot_theta = tan(M_PI / 2.0 - bc->theta_deg * M_PI / 180.0);
+    I.rho_ref = params->rho_ref > 0 ? params->rho_ref : 1.0;
+    I.T_ref = params->T_ref > 0 ? params->T_ref : 0.0;
+    I.inv_n = 1.0 / ((double)nx * ny);
+    e = cudaMemset(c->small, 0, round_up(sizeof(Ctl), kAlign) + round_up(sizeof(Inst), kAlign) + kAlign);
+    if (e == cudaSuccess) e = cudaMemcpy(c->inst_dev, &I, sizeof(Inst), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        int rc = cuda_err(c, e, "lbm_create");
+        lbm_destroy(c);
+        return rc;
+    }
+    auto it = tune_cache().find(std::make_tuple(prec, nx, ny));
+    int threads = 128, rows = 0;
+    if (it != tune_cache().end()) {
+        threads = it->second.first;
+        rows = it->second.second;
+    } else {
+        rows = default_rows(prec, threads, nx, ny);
+    }
+    int rc = ctx_apply_tile(c, threads, rows);
+    if (rc) {
+        lbm_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+static int ctx_upload_inst(lbm_ctx* c) {
+    cudaError_t e = cudaMemcpyAsync(c->inst_dev, &c->inst, sizeof(Inst), cudaMemcpyHostToDevice, c->stream);
+    return cuda_err(c, e, "uploading the domain descriptor");
+}
+
+int lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, const double* uy,
+                    const double* T) {
+    if (!c || !rho || !ux || !uy || !T) return LBM_EINVAL;
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    const size_t N = (size_t)c->nx * c->ny;
+    int rc = ensure_fields(c);
+    if (rc) return rc;
+    double sr = 0.0, sT = 0.0;
+    for (size_t n = 0; n < N; ++n) {
+        sr += rho[n];
+        sT += T[n];
+    }
+    c->inst.rho_ref = c->params.rho_ref > 0 ? c->params.rho_ref : sr / (double)N;
+    c->inst.T_ref = c->params.T_ref > 0 ? c->params.T_ref : sT / (double)N;
+    const double* src[4] = {rho, ux, uy, T};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(c->fields + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "copying the initial fields");
+    if ((rc = ctx_upload_inst(c))) return rc;
+    if (init_launch(c->prec, c->inst_dev, c->inst, c->fields, c->fields + N, c->fields + 2 * N,
+                    c->fields + 3 * N, c->params.w_dot, c->stream))
+        return cuda_err(c, cudaGetLastError(), "init kernel");
+    // state at t = 0: step 0 reads the initial mean density (slot 2)
+    Ctl h;
+    memset(&h, 0, sizeof(h));
+    h.mass[2] = sr;
+    e = cudaMemcpyAsync(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "lbm_init_fields");
+    c->step = 0;
+    c->sticky = LBM_OK;
+    c->initialized = true;
+    c->err.clear();
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+    if (!c || n < 0) return LBM_EINVAL;
+    if (!c->initialized) return set_err(c, LBM_ESTATE, "lbm_step before lbm_init_fields");
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    if (c->sticky) return c->sticky;
+    if (n == 0) return LBM_OK;
+    int rc = enqueue_steps(c->stream, &c->graph, ctx_launch(c), c->prec, c->threads, n, c);
+    if (rc == LBM_OK) c->step += n;
+    return rc;
+}
+
+int lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    if (!c->initialized) return LBM_OK;
+    return ctx_check(c);
+}
+
+int lbm_get_rho_u_T(lbm_ctx* c, double* rho, double* ux, double* uy, double* T) {
+    if (!c) return LBM_EINVAL;
+    if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    int rc = ensure_fields(c);
+    if (rc) return rc;
+    const size_t N = (size_t)c->nx * c->ny;
+    if (fields_launch(c->prec, c->inst_dev, c->inst, c->phys, c->fields, c->fields + N,
+                      c->fields + 2 * N, c->fields + 3 * N, c->stream))
+        return cuda_err(c, cudaGetLastError(), "fields kernel");
+    double* dst[4] = {rho, ux, uy, T};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        if (dst[k])
+            e = cudaMemcpyAsync(dst[k], c->fields + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "copying fields to the host");
+    return ctx_check(c);
+}
+
+int lbm_diagnostics(lbm_ctx* c, double rho_l, double rho_g, int sessile, lbm_diag* out) {
+    if (!c || !out || !(rho_l > rho_g)) return LBM_EINVAL;
+    if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    int rc = ensure_fields(c);
+    if (rc) return rc;
+    const size_t N = (size_t)c->nx * c->ny;
+    if (fields_launch(c->prec, c->inst_dev, c->inst, c->phys, c->fields, c->fields + N,
+                      c->fields + 2 * N, c->fields + 3 * N, c->stream))
+        return cuda_err(c, cudaGetLastError(), "fields kernel");
+    if (diag_launch(c->fields, c->fields + N, c->fields + 2 * N, c->fields + 3 * N, (long long)N,
+                    c->params.cv, rho_l, rho_g, c->diag_out, c->diag_scratch, c->stream))
+        return cuda_err(c, cudaGetLastError(), "diagnostics kernel");
+    double h[8];
+    cudaError_t e = cudaMemcpyAsync(h, c->diag_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "diagnostics");
+    out->mass = h[0];
+    out->energy = h[1];
+    out->liquid_mass = h[2];
+    out->liquid_area = h[3];
+    out->liquid_area_smooth = h[4];
+    out->max_u = h[5];
+    out->nonfinite = (int)h[6];
+    const double fac = sessile ? 8.0 / M_PI : 4.0 / M_PI;
+    out->diameter = sqrt(fac * out->liquid_area);
+    out->diameter_smooth = sqrt(fac * out->liquid_area_smooth);
+    out->step = c->step;
+    return ctx_check(c);
+}
+
+int lbm_get_populations(lbm_ctx* c, double* f, double* g, double* P) {
+    if (!c) return LBM_EINVAL;
+    if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    const size_t N = (size_t)c->nx * c->ny;
+    double* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 15 * N * sizeof(double));
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc(populations)");
+    const int par = (int)(c->step & 1);
+    int rc = LBM_OK;
+    if (pop_get_launch(c->prec, c->inst, par, c->params.w_dot, buf, buf + 9 * N, buf + 14 * N, c->stream))
+        rc = cuda_err(c, cudaGetLastError(), "population kernel");
+    if (!rc && f) e = cudaMemcpyAsync(f, buf, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (!rc && g && e == cudaSuccess)
+        e = cudaMemcpyAsync(g, buf + 9 * N, 5 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (!rc && P && e == cudaSuccess)
+        e = cudaMemcpyAsync(P, buf + 14 * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(buf);
+    if (!rc) rc = cuda_err(c, e, "copying populations");
+    return rc ? rc : ctx_check(c);
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* f, const double* g, const double* P,
+                        long long step, double rho_ave_prev) {
+    if (!c || !f || !g || !P || step < 0) return LBM_EINVAL;
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    const size_t N = (size_t)c->nx * c->ny;
+    if (!c->initialized) {
+        // storage references from the given state
+        double sr = 0.0, sT = 0.0;
+        for (size_t n = 0; n < N; ++n) {
+            double r = 0.0, t = 0.0;
+            for (int i = 0; i < 9; ++i) r += f[i * N + n];
+            for (int i = 0; i < 5; ++i) t += g[i * N + n];
+            sr += r;
+            sT += t;
+        }
+        c->inst.rho_ref = c->params.rho_ref > 0 ? c->params.rho_ref : sr / (double)N;
+        c->inst.T_ref = c->params.T_ref > 0 ? c->params.T_ref : sT / (double)N;
+    }
+    double* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 15 * N * sizeof(double));
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc(populations)");
+    e = cudaMemcpyAsync(buf, f, 9 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + 9 * N, g, 5 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + 14 * N, P, N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    int rc = cuda_err(c, e, "copying populations");
+    if (!rc) rc = ctx_upload_inst(c);
+    if (!rc && pop_set_launch(c->prec, c->inst, (int)(step & 1), c->params.w_dot, buf, buf + 9 * N,
+                              buf + 14 * N, c->stream))
+        rc = cuda_err(c, cudaGetLastError(), "population kernel");
+    Ctl h;
+    memset(&h, 0, sizeof(h));
+    h.step = step;
+    h.mass[(step + 2) % 3] = rho_ave_prev * (double)N;
+    if (!rc) rc = cuda_err(c, cudaMemcpyAsync(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream), "ctl");
+    if (!rc) rc = cuda_err(c, cudaStreamSynchronize(c->stream), "lbm_set_populations");
+    cudaFree(buf);
+    if (rc) return rc;
+    c->step = step;
+    c->sticky = LBM_OK;
+    c->initialized = true;
+    c->err.clear();
+    return LBM_OK;
+}
+
+long long lbm_step_count(const lbm_ctx* c) { return c ? c->step : -1; }
+
+// ---- checkpoint ---------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int version, nx, ny, prec, pitch, pad;
+    long long step;
+    unsigned long long bytes;
+    double mass[3], rho_ref, T_ref;
+    lbm_params params;
+    lbm_bc bc;
+};
+}  // namespace
+
+static size_t ckpt_payload(const lbm_ctx* c) {
+    return 9 * c->lay.planeF + 5 * c->lay.planeG + c->lay.planeP;
+}
+
+int lbm_save(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_EINVAL;
+    if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    Ctl h;
+    if ((rc = ctx_read_ctl(c, &h))) return rc;
+    const int par = (int)(c->step & 1);
+    const size_t bytes = ckpt_payload(c);
+    std::vector<char> buf(bytes);
+    cudaError_t e = cudaMemcpy(buf.data(), c->inst.f[par], 9 * c->lay.planeF, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(buf.data() + 9 * c->lay.planeF, c->inst.g[par], 5 * c->lay.planeG, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(buf.data() + 9 * c->lay.planeF + 5 * c->lay.planeG, c->inst.P[par], c->lay.planeP,
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(c, e, "lbm_save");
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "LBMGB300", 8);
+    hd.version = 1;
+    hd.nx = c->nx;
+    hd.ny = c->ny;
+    hd.prec = c->prec;
+    hd.pitch = c->lay.pitch;
+    hd.step = c->step;
+    hd.bytes = bytes;
+    for (int k = 0; k < 3; ++k) hd.mass[k] = h.mass[k];
+    hd.rho_ref = c->inst.rho_ref;
+    hd.T_ref = c->inst.T_ref;
+    hd.params = c->params;
+    hd.bc = c->bc;
+    uint32_t crc = crc32_update(0, &hd, sizeof(hd));
+    crc = crc32_update(crc, buf.data(), bytes);
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return set_err(c, LBM_EIO, "cannot open checkpoint for writing");
+    bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1 && fwrite(buf.data(), 1, bytes, fp) == bytes &&
+              fwrite(&crc, sizeof(crc), 1, fp) == 1;
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : set_err(c, LBM_EIO, "short write to checkpoint");
+}
+
+int lbm_load(lbm_ctx* c, const char* path) {
+    if (!c || !path) return LBM_EINVAL;
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return set_err(c, LBM_EIO, "cannot open checkpoint");
+    CkptHeader hd;
+    const size_t bytes = ckpt_payload(c);
+    std::vector<char> buf(bytes);
+    uint32_t crc_file = 0;
+    bool ok = fread(&hd, sizeof(hd), 1, fp) == 1;
+    ok = ok && memcmp(hd.magic, "LBMGB300", 8) == 0 && hd.version == 1 && hd.nx == c->nx &&
+         hd.ny == c->ny && hd.prec == c->prec && hd.pitch == c->lay.pitch && hd.bytes == bytes;
+    ok = ok && fread(buf.data(), 1, bytes, fp) == bytes && fread(&crc_file, sizeof(crc_file), 1, fp) == 1;
+    fclose(fp);
+    if (!ok) return set_err(c, LBM_EIO, "checkpoint header or size mismatch");
+    uint32_t crc = crc32_update(0, &hd, sizeof(hd));
+    crc = crc32_update(crc, buf.data(), bytes);
+    if (crc != crc_file) return set_err(c, LBM_EIO, "checkpoint CRC mismatch");
+    const int par = (int)(hd.step & 1);
+    cudaStreamSynchronize(c->stream);
+    cudaError_t e = cudaMemcpy(c->inst.f[par], buf.data(), 9 * c->lay.planeF, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->inst.g[par], buf.data() + 9 * c->lay.planeF, 5 * c->lay.planeG, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->inst.P[par], buf.data() + 9 * c->lay.planeF + 5 * c->lay.planeG, c->lay.planeP,
+                       cudaMemcpyHostToDevice);
+    c->inst.rho_ref = hd.rho_ref;
+    c->inst.T_ref = hd.T_ref;
+    Ctl h;
+    memset(&h, 0, sizeof(h));
+    h.step = hd.step;
+    for (int k = 0; k < 3; ++k) h.mass[k] = hd.mass[k];
+    if (e == cudaSuccess) e = cudaMemcpy(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->inst_dev, &c->inst, sizeof(Inst), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_err(c, e, "lbm_load");
+    c->step = hd.step;
+    c->sticky = LBM_OK;
+    c->initialized = true;
+    c->err.clear();
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    if (c->batch) lbm_batch_detach(c->batch, c);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graph(&c->graph);
+    if (c->units) cudaFree(c->units);
+    if (c->fields) cudaFree(c->fields);
+    if (c->diag_scratch) cudaFree(c->diag_scratch);
+    if (c->diag_out) cudaFree(c->diag_out);
+    if (c->small) cudaFree(c->small);
+    if (c->own_mem && c->mem) cudaFree(c->mem);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+// ---- tile / autotune ------------------------------------------------------
+int lbm_set_tile(lbm_ctx* c, int threads, int rows) {
+    if (!c || (threads != 128 && threads != 256) || rows < 1) return LBM_EINVAL;
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    return ctx_apply_tile(c, threads, std::min(rows, c->ny));
+}
+
+int lbm_get_tile(const lbm_ctx* c, int* threads, int* rows) {
+    if (!c) return LBM_EINVAL;
+    if (threads) *threads = c->threads;
+    if (rows) *rows = c->rows;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_ctx* c, int steps) {
+    if (!c || steps < 1) return LBM_EINVAL;
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    // a scratch domain of the same size, precision and boundaries in a
+    // uniform vapour state, so the caller's state is untouched
+    lbm_ctx* s = nullptr;
+    int rc = lbm_create(c->nx, c->ny, &c->params, &c->bc, c->prec, nullptr, nullptr, 0, &s);
+    if (rc) return set_err(c, rc, "autotune: cannot create the scratch domain");
+    const size_t N = (size_t)c->nx * c->ny;
+    std::vector<double> rho(N, c->inst.rho_ref > 0 ? c->inst.rho_ref : 1.0), z(N, 0.0),
+        T(N, c->inst.T_ref > 0 ? c->inst.T_ref : 0.09);
+    rc = lbm_init_fields(s, rho.data(), z.data(), z.data(), T.data());
+    if (rc) {
+        lbm_destroy(s);
+        return set_err(c, rc, "autotune: init failed");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bt = c->threads, br = c->rows;
+    const int thr_c[2] = {128, 256};
+    const int rows_c[6] = {16, 32, 64, 128, 256, 512};
+    for (int ti = 0; ti < 2; ++ti)
+        for (int ri = 0; ri < 6; ++ri) {
+            int rows = std::min(rows_c[ri], c->ny);
+            if (ri > 0 && rows_c[ri - 1] >= c->ny) continue;
+            if (ctx_apply_tile(s, thr_c[ti], rows)) continue;
+            lbm_step(s, 2);
+            cudaEventRecord(e0, s->stream);
+            lbm_step(s, steps);
+            cudaEventRecord(e1, s->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bt = thr_c[ti];
+                br = rows;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lbm_destroy(s);
+    tune_cache()[std::make_tuple(c->prec, c->nx, c->ny)] = std::make_pair(bt, br);
+    return ctx_apply_tile(c, bt, br);
+}
+
+// ---- batch ---------------------------------------------------------------
+static int batch_rebuild(lbm_batch* b) {
+    drop_graph(&b->graph);
+    if (b->insts) cudaFree(b->insts);
+    if (b->units) cudaFree(b->units);
+    b->insts = nullptr;
+    b->units = nullptr;
+    b->n_units = 0;
+    if (b->members.empty()) return LBM_OK;
+    std::vector<Inst> hi;
+    std::vector<Unit> us;
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        hi.push_back(b->members[i]->inst);
+        build_units(b->members[i]->inst, (int)i, b->threads, std::min(b->rows, b->members[i]->ny), us);
+    }
+    // longest-first is not needed: units of one batch are near-equal in size;
+    // keep domain order so neighbouring units share halos in L2
+    cudaError_t e = cudaMalloc(&b->insts, hi.size() * sizeof(Inst));
+    if (e == cudaSuccess) e = cudaMalloc(&b->units, us.size() * sizeof(Unit));
+    if (e == cudaSuccess) e = cudaMemcpy(b->insts, hi.data(), hi.size() * sizeof(Inst), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->units, us.data(), us.size() * sizeof(Unit), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+    b->n_units = (int)us.size();
+    int ctas = 1;
+    size_t smem = 0;
+    step_occupancy(b->prec, b->threads, &ctas, &smem);
+    b->grid = (int)std::min<long long>((long long)b->n_units, (long long)std::max(ctas, 1) * num_sms());
+    return LBM_OK;
+}
+
+int lbm_batch_create(void* stream, lbm_batch** out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ENOMEM;
+    cudaError_t e = cudaSuccess;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        b->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->sched, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->sched, 0, 2 * sizeof(unsigned));
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return LBM_ECUDA;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_attach(lbm_batch* b, lbm_ctx* c) {
+    if (!b || !c) return LBM_EINVAL;
+    if (c->batch) return set_err(c, LBM_ESTATE, "context already in a batch");
+    if (!c->initialized) return set_err(c, LBM_ESTATE, "attach after lbm_init_fields");
+    if (b->members.empty()) {
+        b->prec = c->prec;
+        b->params = c->params;
+        b->phys = c->phys;
+        b->threads = 128;
+        b->rows = 64;
+    } else if (b->prec != c->prec || !same_physics(b->params, c->params)) {
+        return set_err(c, LBM_EINVAL, "batch members must share precision and physics");
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(b->stream);
+    b->members.push_back(c);
+    c->batch = b;
+    int rc = batch_rebuild(b);
+    if (rc) {
+        b->members.pop_back();
+        c->batch = nullptr;
+        batch_rebuild(b);
+    }
+    return rc;
+}
+
+int lbm_batch_detach(lbm_batch* b, lbm_ctx* c) {
+    if (!b || !c || c->batch != b) return LBM_EINVAL;
+    cudaStreamSynchronize(b->stream);
+    b->members.erase(std::remove(b->members.begin(), b->members.end(), c), b->members.end());
+    c->batch = nullptr;
+    return batch_rebuild(b);
+}
+
+int lbm_batch_size(const lbm_batch* b) { return b ? (int)b->members.size() : 0; }
+
+int lbm_batch_step(lbm_batch* b, int n) {
+    if (!b || n < 0) return LBM_EINVAL;
+    if (b->members.empty() || n == 0) return LBM_OK;
+    for (lbm_ctx* c : b->members)
+        if (c->sticky) return c->sticky;
+    StepLaunch L;
+    L.insts = b->insts;
+    L.units = b->units;
+    L.n_units = b->n_units;
+    L.n_inst = (int)b->members.size();
+    L.sched = b->sched;
+    L.grid = b->grid;
+    L.phys = b->phys;
+    int rc = enqueue_steps(b->stream, &b->graph, L, b->prec, b->threads, n, b->members[0]);
+    if (rc == LBM_OK)
+        for (lbm_ctx* c : b->members) c->step += n;
+    return rc;
+}
+
+int lbm_batch_sync(lbm_batch* b) {
+    if (!b) return LBM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return LBM_ECUDA;
+    int first = LBM_OK;
+    for (lbm_ctx* c : b->members) {
+        Ctl h;
+        if (cudaMemcpy(&h, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ECUDA;
+        if (h.err && c->sticky == LBM_OK) {
+            c->sticky = map_device_err(h.err);
+            c->err = "device error in batched step";
+        }
+        if (c->sticky && first == LBM_OK) first = c->sticky;
+    }
+    return first;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (lbm_ctx* c : b->members) c->batch = nullptr;
+    b->members.clear();
+    drop_graph(&b->graph);
+    if (b->insts) cudaFree(b->insts);
+    if (b->units) cudaFree(b->units);
+    if (b->sched) cudaFree(b->sched);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

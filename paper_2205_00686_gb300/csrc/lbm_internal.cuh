@@ -1,0 +1,204 @@
+// Internal definitions shared by the CUDA translation units of the library:
+// device-resident descriptors, the per-launch physics constants and the
+// closed-form pieces of the coupled step (Peng-Robinson EOS of Section 2,
+// Eq. 10; the pseudopotential psi; (dp/dT)_rho used by Q of Eq. 20).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// flow / thermal boundary kinds (same values as the public header)
+enum { PERIODIC = 0, WALL = 1, OPEN = 2 };
+enum { T_PERIODIC = 0, T_DIRICHLET = 1, T_ADIABATIC = 2 };
+enum { EW = 0, EE = 1, ES = 2, EN = 3 };
+
+// sticky device error bits
+enum { ERR_PSI = 1, ERR_NONFINITE = 2 };
+
+// Device-resident control block of one domain: the device-side step counter
+// read by every launch, the three-slot ring of per-step density sums used by
+// the buoyancy force (step n accumulates sum rho(n) into slot n % 3 and reads
+// slot (n - 1) % 3), and the sticky error word.
+struct Ctl {
+    long long step;
+    double mass[3];
+    int err;
+    int pad;
+};
+
+// One domain as seen by the kernels.  Populations are stored as deviations
+// f_i - w_i rho_ref and g_i - w^_i T_ref, SoA planes [q][ny][pitch].
+struct Inst {
+    void* f[2];
+    void* g[2];
+    void* P[2];
+    Ctl* ctl;
+    int nx, ny, pitch;
+    int flow[4], therm[4];
+    int heater_x0, heater_x1;
+    double T_edge[4], T_heater, cot_theta;
+    double rho_ref, T_ref, inv_n;
+};
+
+// A work unit of the fused step: output columns [x0, x1), rows [y0, y1) of
+// domain `inst`.
+struct Unit {
+    int inst, x0, x1, y0, y1;
+};
+
+// Physical constants shared by every domain of a launch, already combined
+// into the factors the kernels use.
+template <class R>
+struct Phys {
+    // EOS: p = rho Rg T/(1 - b rho) - a h^2 rho^2/(1 + 2 b rho - b^2 rho^2),
+    // h = 1 + kpr (1 - sqrt(T/Tc))
+    R a, b, Rg, kpr, inv_Tc, akTc;   // akTc = a kpr / Tc
+    R two_over_G, negG;
+    // D2Q9 MRT rates and Li forcing
+    R s_e, s_eps, s_q, s_p;
+    R hs_e, hs_eps, hs_q, hs_p;      // 1 - s/2
+    R sig_e, sig_eps;                // sigma / (1/s - 1/2)
+    // D2Q5
+    R cv, w_dot, w5_0, w5_1, vs1_cs2h, vs3, vs4;   // vs1_cs2h = vs1 / cs2h
+    R one_m_vs1, one_m_vs4;
+    R gravity;
+    int frozen_flow, frozen_thermal;
+};
+
+struct PhysD {
+    double a, b, Rg, omega, G, sigma;
+    double s_e, s_eps, s_q, s_p;
+    double cv, w_dot, vs1, vs3, vs4;
+    double gravity;
+    int frozen_flow, frozen_thermal;
+};
+
+template <class R>
+inline Phys<R> make_phys(const PhysD& d) {
+    Phys<R> p;
+    double kpr = 0.37464 + 1.54226 * d.omega - 0.26992 * d.omega * d.omega;
+    double Tc = 0.0778 * d.a / (0.45724 * d.b * d.Rg);
+    p.a = (R)d.a;
+    p.b = (R)d.b;
+    p.Rg = (R)d.Rg;
+    p.kpr = (R)kpr;
+    p.inv_Tc = (R)(1.0 / Tc);
+    p.akTc = (R)(d.a * kpr / Tc);
+    p.two_over_G = (R)(2.0 / d.G);
+    p.negG = (R)(-d.G);
+    p.s_e = (R)d.s_e;
+    p.s_eps = (R)d.s_eps;
+    p.s_q = (R)d.s_q;
+    p.s_p = (R)d.s_p;
+    p.hs_e = (R)(1.0 - 0.5 * d.s_e);
+    p.hs_eps = (R)(1.0 - 0.5 * d.s_eps);
+    p.hs_q = (R)(1.0 - 0.5 * d.s_q);
+    p.hs_p = (R)(1.0 - 0.5 * d.s_p);
+    p.sig_e = (R)(d.sigma / (1.0 / d.s_e - 0.5));
+    p.sig_eps = (R)(d.sigma / (1.0 / d.s_eps - 0.5));
+    p.cv = (R)d.cv;
+    p.w_dot = (R)d.w_dot;
+    p.w5_0 = (R)(1.0 - d.w_dot);
+    p.w5_1 = (R)(0.25 * d.w_dot);
+    p.vs1_cs2h = (R)(d.vs1 / (0.5 * d.w_dot));
+    p.vs3 = (R)d.vs3;
+    p.vs4 = (R)d.vs4;
+    p.one_m_vs1 = (R)(1.0 - d.vs1);
+    p.one_m_vs4 = (R)(1.0 - d.vs4);
+    p.gravity = (R)d.gravity;
+    p.frozen_flow = d.frozen_flow;
+    p.frozen_thermal = d.frozen_thermal;
+    return p;
+}
+
+// ---- storage conversions ------------------------------------------------
+__device__ __forceinline__ float ld_st(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ld_st(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_st(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ void st_st(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_st(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st_st(__half* p, float v) { *p = __float2half_rn(v); }
+
+// ---- arithmetic helpers (precision-generic) -------------------------------
+__device__ __forceinline__ float rsq(float x) { return sqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return sqrt(x); }
+__device__ __forceinline__ float rabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double rabs(double x) { return fabs(x); }
+
+// Peng-Robinson pressure (Eq. 10) and psi^2 = 2 (p_EOS - rho/3) / G.
+template <class R>
+__device__ __forceinline__ R eos_p(const Phys<R>& P, R rho, R T) {
+    R st = rsq(T * P.inv_Tc);
+    R h = R(1) + P.kpr * (R(1) - st);
+    R br = P.b * rho;
+    return rho * P.Rg * T / (R(1) - br) - P.a * h * h * rho * rho / (R(1) + R(2) * br - br * br);
+}
+
+// (dp_EOS/dT)_rho = rho Rg/(1 - b rho) + a k h rho^2 / (sqrt(T/Tc) Tc (1 + 2 b rho - b^2 rho^2))
+template <class R>
+__device__ __forceinline__ R eos_dpdT(const Phys<R>& P, R rho, R T) {
+    R st = rsq(T * P.inv_Tc);
+    R h = R(1) + P.kpr * (R(1) - st);
+    R br = P.b * rho;
+    return rho * P.Rg / (R(1) - br) + P.akTc * h * rho * rho / (st * (R(1) + R(2) * br - br * br));
+}
+
+template <class R>
+__device__ __forceinline__ R psi2_of(const Phys<R>& P, R rho, R T) {
+    return P.two_over_G * (eos_p(P, rho, T) - rho * R(1.0 / 3.0));
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// wall / Dirichlet temperature along an edge, with the heater segment
+__device__ __forceinline__ double wall_T(const Inst& I, int edge, int gx) {
+    if (edge == ES && gx >= I.heater_x0 && gx < I.heater_x1) return I.T_heater;
+    return I.T_edge[edge];
+}
+
+// Per-instance storage types by precision code
+template <int PREC> struct Types;
+template <> struct Types<0> { typedef double R; typedef double TF; typedef double TG; };
+template <> struct Types<1> { typedef float R; typedef float TF; typedef float TG; };
+template <> struct Types<2> { typedef float R; typedef float TF; typedef __half TG; };
+
+inline size_t elem_f(int prec) { return prec == 0 ? 8 : 4; }
+inline size_t elem_g(int prec) { return prec == 0 ? 8 : (prec == 1 ? 4 : 2); }
+inline size_t elem_P(int prec) { return prec == 0 ? 8 : 4; }
+
+// ---- launchers implemented in the .cu files ------------------------------
+struct StepLaunch {
+    Inst* insts;
+    const Unit* units;
+    int n_units;
+    int n_inst;
+    unsigned* sched;   // [0] next unit, [1] finished CTAs
+    int grid;
+    PhysD phys;
+};
+
+int step_launch(int prec, int threads, const StepLaunch& L, cudaStream_t st);
+int step_occupancy(int prec, int threads, int* ctas_per_sm, size_t* smem_bytes);
+
+int init_launch(int prec, const Inst* I_dev, const Inst& I, const double* rho, const double* ux,
+                const double* uy, const double* T, double w_dot, cudaStream_t st);
+int fields_launch(int prec, const Inst* I_dev, const Inst& I, const PhysD& phys, double* rho,
+                  double* ux, double* uy, double* T, cudaStream_t st);
+int pop_get_launch(int prec, const Inst& I, int parity, double w_dot, double* f, double* g,
+                   double* P, cudaStream_t st);
+int pop_set_launch(int prec, const Inst& I, int parity, double w_dot, const double* f,
+                   const double* g, const double* P, cudaStream_t st);
+// reduction of device fields into 8 doubles + a nonfinite count; `scratch`
+// holds diag_scratch_bytes(n) bytes
+size_t diag_scratch_bytes(long long n);
+int diag_launch(const double* rho, const double* ux, const double* uy, const double* T,
+                long long n, double cv, double rho_l, double rho_g, double* out9,
+                void* scratch, cudaStream_t st);
+
+}  // namespace lbm
