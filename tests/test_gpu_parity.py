@@ -99,15 +99,23 @@ def test_graph_replay_matches_single_launches():
 
 
 def test_tiles_give_identical_results():
+    """The segment height never changes the arithmetic of a node: results are
+    bitwise equal for one kernel instantiation.  The 128- and 256-thread
+    instantiations are compiled separately (the compiler may contract
+    multiply-adds differently), so across them the results agree to FP32
+    rounding."""
     c = P.droplet_case(300, 90, P.bc_variants()["open_dirichlet"])
-    ref = None
-    for tile in [(128, 16), (128, 90), (256, 33), (256, 8)]:
+    ref = {}
+    for tile in [(128, 16), (128, 90), (128, 7), (256, 33), (256, 8), (256, 90)]:
         d = P.run_gpu(c, 40, "fp32", tile=tile)
         f, g, _ = d.populations()
-        if ref is None:
-            ref = (f, g)
+        if tile[0] not in ref:
+            ref[tile[0]] = (f, g)
         else:
-            assert np.array_equal(ref[0], f) and np.array_equal(ref[1], g), tile
+            r = ref[tile[0]]
+            assert np.array_equal(r[0], f) and np.array_equal(r[1], g), tile
+    assert P.rel_err(ref[128][0], ref[256][0]) < 1e-6
+    assert P.rel_err(ref[128][1], ref[256][1]) < 1e-6
 
 
 def test_diagnostics_match_oracle():
@@ -129,8 +137,7 @@ def test_set_populations_roundtrip_and_continue():
     f, g, Pp = o.populations()
     import paper_2205_00686_gb300 as lbm
     d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp64")
-    rho_ave = o.fields()[0].mean()  # not the lagged value: recompute it below
-    # the oracle keeps the mean of step 29's density for step 30
+    # the buoyancy force of step 30 uses the mean density of step 29
     o2 = P.run_oracle(c, 29)
     rho_ave = o2.fields()[0].mean()
     d.set_populations(f, g, Pp, 30, rho_ave)
