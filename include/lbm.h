@@ -39,6 +39,7 @@ extern "C" {
 #define LBM_ECUDA (-5)       /* a CUDA runtime call failed                     */
 #define LBM_EIO (-6)         /* checkpoint file could not be read or written  */
 #define LBM_ESTATE (-7)      /* call out of order (e.g. step before init)     */
+#define LBM_ETOOBIG (-8)     /* size beyond a fixed capacity (no-alloc entry)  */
 
 /* ---- precision of storage and arithmetic ------------------------------- */
 typedef enum {
@@ -221,6 +222,36 @@ void lbm_batch_destroy(lbm_batch* b);
 int lbm_set_tile(lbm_ctx* ctx, int threads, int rows);
 int lbm_get_tile(const lbm_ctx* ctx, int* threads, int* rows);
 int lbm_autotune(lbm_ctx* ctx, int steps_per_trial);
+
+/* ---- diagnostics without any allocation -------------------------------- *
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory: a process whose GPU memory is owned by another
+ * framework's pool, a loop that cannot afford cudaMalloc's implicit device
+ * synchronisation, or a plugin that is handed device pointers and a stream
+ * and nothing else.  It computes the same sums as lbm_diagnostics, but from
+ * device field arrays the caller provides, and keeps its scratch (per-block
+ * partial sums) in one fixed-size array inside the library (256 KB per GPU,
+ * held from the first call until the process exits) instead of allocating.
+ *
+ *  rho, ux, uy, T: device arrays of n doubles each (any node order).
+ *  out7: device array receiving 7 doubles: sum rho, sum rho cv T, liquid mass
+ *        and liquid node count above (rho_l + rho_g)/2, the smooth liquid
+ *        area sum clamp((rho - rho_g)/(rho_l - rho_g), 0, 1), max |u| and the
+ *        number of nodes with a non-finite value.
+ *  stream: cudaStream_t as void* (NULL: the legacy default stream); the call
+ *        is asynchronous on it.
+ * Returns LBM_EINVAL for NULL pointers, n < 0 or rho_l <= rho_g, LBM_ETOOBIG
+ * for n > LBM_NOALLOC_MAX_NODES (the capacity of the fixed scratch), and
+ * LBM_ECUDA if the CUDA runtime refuses a call.  It never calls cudaMalloc or
+ * cudaFree.  The first call on each device looks up the device address of the
+ * scratch array for that device (with that device current); make that first
+ * call before any stream capture.  All calls on a device share the array:
+ * calls whose kernels may overlap on the GPU (unordered streams) race, so
+ * keep them on one stream. */
+#define LBM_NOALLOC_MAX_NODES 33554432LL
+int lbm_diag_reduce_noalloc(const double* rho, const double* ux, const double* uy,
+                            const double* T, long long n, double cv, double rho_l,
+                            double rho_g, double* out7, void* stream);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,8 @@ LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ENONFINITE, LBM_EPSI, LBM_ECUDA, LBM_EIO, LBM_ESTATE = (
     0, -1, -2, -3, -4, -5, -6, -7)
+LBM_ETOOBIG = -8
+LBM_NOALLOC_MAX_NODES = 33554432
 LBM_FP64, LBM_FP32, LBM_FP32_G16 = 0, 1, 2
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp32_g16": LBM_FP32_G16}
 LBM_PERIODIC, LBM_WALL, LBM_OPEN = 0, 1, 2
@@ -35,7 +37,7 @@ ABI_FUNCTIONS = (
     "lbm_step_count", "lbm_sync", "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
     "lbm_batch_create", "lbm_batch_attach", "lbm_batch_detach", "lbm_batch_size",
     "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy", "lbm_set_tile", "lbm_get_tile",
-    "lbm_autotune",
+    "lbm_autotune", "lbm_diag_reduce_noalloc",
 )
 
 
@@ -110,6 +112,9 @@ def lib():
             "lbm_get_tile": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                              ctypes.c_int),
             "lbm_autotune": ([_vp, ctypes.c_int], ctypes.c_int),
+            "lbm_diag_reduce_noalloc": ([_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, _vp, _vp],
+                                        ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -260,6 +265,13 @@ class Domain:
     @property
     def last_error(self) -> str:
         return lib().lbm_last_error(self._h).decode()
+
+
+def lbm_diag_reduce_noalloc(rho, ux, uy, T, n, cv, rho_l, rho_g, out7, stream=None) -> int:
+    """Diagnostics sums of device field arrays without allocating (device
+    pointers as ints, e.g. torch's data_ptr()); returns the ABI's code."""
+    return int(lib().lbm_diag_reduce_noalloc(rho, ux, uy, T, int(n), float(cv), float(rho_l),
+                                             float(rho_g), out7, stream))
 
 
 class Batch:
