@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--size", type=int, default=NX,
+                    help="domain side (default 4096; smaller sides for profiler captures)")
     return ap.parse_args()
 
 
@@ -210,7 +212,7 @@ def run_ours(args):
     if rank == 0 or world > 1:
         _build.build()
     stream = torch.cuda.Stream()
-    case = make_case()
+    case = make_case(args.size)
     N = case.nx * case.ny
 
     dom = lbm.Domain(case.nx, case.ny, case.params, case.bc, prec="fp32",
@@ -295,8 +297,10 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "droplet evaporation, open outflow, Dirichlet 0.95Tc edges, "
-                               "R=640, 4096x4096, FP32 fused step",
-                   "nx": NX, "ny": NY, "l2": "inputs larger than L2 (2 GiB state)",
+                               "R=%g, %dx%d, FP32 fused step" % (640.0 * case.nx / 4096.0,
+                                                                  case.nx, case.ny),
+                   "nx": case.nx, "ny": case.ny,
+                   "l2": "inputs larger than L2 (%.2f GiB state)" % (2 * 60.0 * N / 2 ** 30),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "tile": list(dom.tile())},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
