@@ -130,7 +130,8 @@ size_t lbm_state_bytes(int nx, int ny, int prec);
  *          lbm_state_bytes(nx, ny, prec) bytes, 256-byte aligned, to hold the
  *          state (e.g. from a PyTorch allocation); NULL to let the library
  *          allocate.  The caller keeps it alive until lbm_destroy.
- * Errors: LBM_EINVAL (sizes < 1, bad precision, unsupported boundary
+ * Errors: LBM_EINVAL (sizes < 1, 9 * ny * round_up(nx, 64) >= 2^31 (e.g.
+ * beyond about 15000 x 15000), bad precision, unsupported boundary
  * combination, non-positive cv / nu / lambda, w_dot outside (0,1)),
  * LBM_ENOMEM, LBM_ECUDA.  *out is NULL on failure. */
 int lbm_create(int nx, int ny, const lbm_params* params, const lbm_bc* bc, int prec,

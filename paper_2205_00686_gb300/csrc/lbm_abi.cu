@@ -133,15 +133,17 @@ void build_units(const Inst& I, int inst_index, int threads, int rows, std::vect
         }
 }
 
-// default segment height: enough units to fill the GPU twice, 16..256 rows
+// default segment height: 64 rows (7 pipeline-fill rows per segment stay
+// ~10% of the sweep) unless that leaves the persistent grid without at least
+// one unit per resident CTA; never below 8
 int default_rows(int prec, int threads, int nx, int ny) {
     int ctas = 1;
     size_t smem = 0;
     step_occupancy(prec, threads, &ctas, &smem);
     const long long slots = (long long)std::max(ctas, 1) * num_sms();
     const int strips = (nx + threads - 9) / (threads - 8);
-    int rows = 256;
-    while (rows > 16 && (long long)strips * ((ny + rows - 1) / rows) < 2 * slots) rows /= 2;
+    int rows = 64;
+    while (rows > 8 && (long long)strips * ((ny + rows - 1) / rows) < slots) rows /= 2;
     return std::max(1, std::min(rows, ny));
 }
 
@@ -337,6 +339,8 @@ int lbm_create(int nx, int ny, const lbm_params* params, const lbm_bc* bc, int p
     *out = nullptr;
     if (nx < 1 || ny < 1 || !params || !bc || prec < 0 || prec > 2) return LBM_EINVAL;
     if (nx > (1 << 20) || ny > (1 << 20)) return LBM_EINVAL;
+    // the kernels address the 9 planes of f with 32-bit element offsets
+    if ((unsigned long long)layout_for(nx, ny, prec).pitch * ny * 9ull >= (1ull << 31)) return LBM_EINVAL;
     if (!bc_valid(nx, ny, bc)) return LBM_EINVAL;
     if (!(params->cv > 0) || !(params->nu > 0) || !(params->lambda > 0) ||
         !(params->w_dot > 0 && params->w_dot < 1) || params->G == 0.0 || !(params->b > 0) ||

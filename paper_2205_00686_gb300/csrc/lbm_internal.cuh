@@ -62,7 +62,7 @@ struct Phys {
     R hs_e, hs_eps, hs_q, hs_p;      // 1 - s/2
     R sig_e, sig_eps;                // sigma / (1/s - 1/2)
     // D2Q5
-    R cv, w_dot, w5_0, w5_1, vs1_cs2h, vs3, vs4;   // vs1_cs2h = vs1 / cs2h
+    R cv, inv_cv, w_dot, w5_0, w5_1, vs1_cs2h, vs3, vs4;   // vs1_cs2h = vs1 / cs2h
     R one_m_vs1, one_m_vs4;
     R gravity;
     int frozen_flow, frozen_thermal;
@@ -100,6 +100,7 @@ inline Phys<R> make_phys(const PhysD& d) {
     p.sig_e = (R)(d.sigma / (1.0 / d.s_e - 0.5));
     p.sig_eps = (R)(d.sigma / (1.0 / d.s_eps - 0.5));
     p.cv = (R)d.cv;
+    p.inv_cv = (R)(1.0 / d.cv);
     p.w_dot = (R)d.w_dot;
     p.w5_0 = (R)(1.0 - d.w_dot);
     p.w5_1 = (R)(0.25 * d.w_dot);
@@ -123,10 +124,25 @@ __device__ __forceinline__ void st_st(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st_st(__half* p, float v) { *p = __float2half_rn(v); }
 
 // ---- arithmetic helpers (precision-generic) -------------------------------
+// FP64 keeps IEEE division and square root (parity with the FP64 oracle to
+// ~1e-13); FP32 uses the hardware approximations (rcp.approx / sqrt.approx,
+// relative error ~2^-23), well inside the FP32 tolerance.
 __device__ __forceinline__ float rsq(float x) { return sqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return sqrt(x); }
 __device__ __forceinline__ float rabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double rabs(double x) { return fabs(x); }
+__device__ __forceinline__ float f_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double f_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float f_sqrt(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
 
 // Peng-Robinson pressure (Eq. 10) and psi^2 = 2 (p_EOS - rho/3) / G.
 template <class R>
@@ -149,6 +165,22 @@ __device__ __forceinline__ R eos_dpdT(const Phys<R>& P, R rho, R T) {
 template <class R>
 __device__ __forceinline__ R psi2_of(const Phys<R>& P, R rho, R T) {
     return P.two_over_G * (eos_p(P, rho, T) - rho * R(1.0 / 3.0));
+}
+
+// psi^2 and T (dp/dT)_rho of one node from shared sub-expressions:
+// st = sqrt(T/Tc), h = 1 + k (1 - st), ib = 1/(1 - b rho),
+// r2id = rho^2 / (1 + 2 b rho - b^2 rho^2)
+template <class R>
+__device__ __forceinline__ void eos_node(const Phys<R>& P, R rho, R T, R* psi2, R* TdpdT) {
+    const R st = f_sqrt(T * P.inv_Tc);
+    const R h = R(1) + P.kpr * (R(1) - st);
+    const R br = P.b * rho;
+    const R ib = f_rcp(R(1) - br);
+    const R r2id = rho * rho * f_rcp(R(1) + br * (R(2) - br));
+    const R rRib = rho * P.Rg * ib;
+    const R p = rRib * T - P.a * h * h * r2id;
+    *psi2 = P.two_over_G * (p - rho * R(1.0 / 3.0));
+    *TdpdT = T * (rRib + P.akTc * h * r2id * f_rcp(st));
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) {

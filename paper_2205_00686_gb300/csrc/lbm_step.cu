@@ -10,7 +10,8 @@
 // stages skewed in rows and keeps each stage's results in small shared-memory
 // rings three rows deep:
 //
-//   phase alpha of iteration k:  A(k)    load f, g, P of row k; rho, T, j, psi
+//   phase alpha of iteration k:  A(k)    load f, g, P of row k; rho, T, j,
+//                                        psi and T (dp/dT)_rho (Eq. 10)
 //                                C(k-3)  div u, grad T (Eqs. 49-50), Q, S,
 //                                        D2Q5 collision -> g*
 //                                D9(k-3) pull-stream f* into row k-3, store
@@ -34,22 +35,43 @@
 
 namespace lbm {
 
+template <class R>
+struct Vec2;
+template <>
+struct Vec2<float> { typedef float2 T; };
+template <>
+struct Vec2<double> { typedef double2 T; };
+template <class R>
+struct Vec4;
+template <>
+struct Vec4<float> { typedef float4 T; };
+template <>
+struct Vec4<double> { typedef double4 T; };
+
 template <class R, int NT>
 struct StepSmem {
     R psi[3][NT];
     R rho[3][NT];
     R T[3][NT];
-    R ux[3][NT];
-    R uy[3][NT];
-    R fs[3][9][NT];    // post-collision f (deviation form)
-    R gs[3][5][NT];    // post-collision g (deviation form)
-    R own[5][7][NT];   // per column: g_dev[5], rho, P^{n-1} of the row
+    typename Vec2<R>::T u[3][NT];
+    R fs[3][9][NT];     // post-collision f (deviation form)
+    R gs[3][5][NT];     // post-collision g (deviation form)
+    // per column and row: g_dev[0..4], rho, P^{n-1}, T (dp/dT)_rho
+    typename Vec4<R>::T own[5][2][NT];
     double red[NT / 32];
     int unit;
 };
 
-__device__ __forceinline__ int slot3(int r) { return (r + 6) % 3; }
-__device__ __forceinline__ int slot5(int r) { return (r + 10) % 5; }
+// ghost-layer psi of a wall (Section 3.3): rho_ghost = rho(layer 2) +
+// tan(pi/2 - theta) |rho(x+1, layer 1) - rho(x-1, layer 1)|
+template <class R>
+__device__ __forceinline__ R ghost_psi(const Phys<R>& P, R rho_far, R rho_p, R rho_m, R cot, R Tg,
+                                       int* err) {
+    const R rg = rho_far + cot * rabs(rho_p - rho_m);
+    const R q2 = psi2_of(P, rg, Tg);
+    if (!(q2 >= R(0))) *err |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
+    return f_sqrt(q2);
+}
 
 template <int PREC, int NT>
 __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
@@ -58,6 +80,8 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
     typedef typename Types<PREC>::R R;
     typedef typename Types<PREC>::TF TF;
     typedef typename Types<PREC>::TG TG;
+    typedef typename Vec2<R>::T R2;
+    typedef typename Vec4<R>::T R4;
 
     const int t = threadIdx.x;
     const int nx = I.nx, ny = I.ny, pitch = I.pitch;
@@ -66,7 +90,8 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
     const long long step = __ldcg(&I.ctl->step);
     const int par = (int)(step & 1);
     const bool first = step == 0;
-    const size_t plane = (size_t)ny * pitch;
+    // plane stride in elements; lbm_create keeps 9 planes within 2^31 elements
+    const unsigned plane = (unsigned)ny * (unsigned)pitch;
     const TF* __restrict__ fsrc = (const TF*)I.f[par];
     const TG* __restrict__ gsrc = (const TG*)I.g[par];
     const R* __restrict__ Psrc = (const R*)I.P[par];
@@ -85,110 +110,139 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
     const int X = x0 - 4 + t;
     const bool colvalid = perx || (X >= 0 && X < nx);
     const int gx = perx ? wrapi(X, nx) : X;
-    auto extx = [&](int Xp) { return perx ? Xp : min(max(Xp, 0), nx - 1); };
-    auto sidx = [&](int Xp) { return extx(Xp) - x0 + 4; };
-    auto gcol = [&](int c) { return perx ? wrapi(x0 - 4 + c, nx) : x0 - 4 + c; };
-    const int xl1 = sidx(X - 1), xr1 = sidx(X + 1);
-    const int cLL = sidx(extx(X - 1) - 1), cLR = sidx(extx(X - 1) + 1);
-    const int cRL = sidx(extx(X + 1) - 1), cRR = sidx(extx(X + 1) + 1);
+    // window index of a column one or two away, clamped at open x edges
+    const int xm1 = perx ? X - 1 : min(max(X - 1, 0), nx - 1);
+    const int xp1 = perx ? X + 1 : min(max(X + 1, 0), nx - 1);
+    const int xl1 = xm1 - x0 + 4, xr1 = xp1 - x0 + 4;
+    const int cLL = (perx ? xm1 - 1 : min(max(xm1 - 1, 0), nx - 1)) - x0 + 4;
+    const int cRR = (perx ? xp1 + 1 : min(max(xp1 + 1, 0), nx - 1)) - x0 + 4;
+    const int cLR = (perx ? xm1 + 1 : min(max(xm1 + 1, 0), nx - 1)) - x0 + 4;
+    const int cRL = (perx ? xp1 - 1 : min(max(xp1 - 1, 0), nx - 1)) - x0 + 4;
     const bool inB = colvalid && X >= x0 - 2 && X < x1 + 2;
     const bool inC = colvalid && X >= x0 - 1 && X < x1 + 1;
     const bool inD = X >= x0 && X < x1;
     const bool left_edge = !perx && X == 0;
     const bool right_edge = !perx && X == nx - 1;
 
-    auto rowvalid = [&](int r) { return pery || (r >= 0 && r < ny); };
-    auto grow = [&](int r) { return pery ? wrapi(r, ny) : r; };
+    // thermal boundary values, as deviations from T_ref (halfway
+    // anti-bounce-back A = -g*_opp + 2 w^ (T_w - T_ref) in deviation form)
+    const bool dirW = I.therm[EW] == T_DIRICHLET, dirE = I.therm[EE] == T_DIRICHLET;
+    const bool dirS = I.therm[ES] == T_DIRICHLET, dirN = I.therm[EN] == T_DIRICHLET;
+    R twW = R(0), twE = R(0), twS = R(0), twN = R(0);
+    R TgS_l = R(0), TgS_c = R(0), TgS_r = R(0), TgN = R(0);
+    if (!perx) {
+        twW = (R)(I.T_edge[EW] - I.T_ref);
+        twE = (R)(I.T_edge[EE] - I.T_ref);
+    }
+    if (!pery && inD) {
+        twS = (R)(wall_T(I, ES, gx) - I.T_ref);
+        twN = (R)(I.T_edge[EN] - I.T_ref);
+    }
+    if (wallS || wallN) {
+        // global columns of the window indices xl1, t, xr1
+        const int gl = perx ? wrapi(X - 1, nx) : xm1;
+        const int gr = perx ? wrapi(X + 1, nx) : xp1;
+        TgS_l = (R)wall_T(I, ES, gl);
+        TgS_c = (R)wall_T(I, ES, gx);
+        TgS_r = (R)wall_T(I, ES, gr);
+        TgN = (R)I.T_edge[EN];
+    }
+    const R twS2 = R(2) * P.w5_1 * twS, twN2 = R(2) * P.w5_1 * twN;
+    const R twW2 = R(2) * P.w5_1 * twW, twE2 = R(2) * P.w5_1 * twE;
 
     // registers carried from A(k-1) to B(k-1)
-    R fp[9], rhop = R(1), rhodp = R(0), jxp = R(0), jyp = R(0), Tp = R(0), psip = R(0);
+    R fp[9], rhop = R(1), rhodp = R(0), jxp = R(0), jyp = R(0), psip = R(0), irp = R(1);
 #pragma unroll
     for (int q = 0; q < 9; ++q) fp[q] = R(0);
-    double mass_acc = 0.0;
+    R mass_acc = R(0);   // this thread's output densities (summed in double per unit)
     int errbits = 0;
 
+    // rotating ring slots: a0 = slot of row k, a1 = row k-1, a2 = row k-2
+    // (ring of 3, so row k-3 is a0 again); b0 = slot of row k in the ring of 5
+    int a0 = 0, a1 = 2, a2 = 1, b0 = 0;
+    // wrapped row of k for loads
+    int kw = pery ? wrapi(y0 - 3, ny) : y0 - 3;
+
+    // populations of the row A works on, loaded one phase ahead (the loads
+    // of row k are issued before B(k-1) so their latency overlaps it)
+    R fa[9], ga[5], pa = R(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) fa[q] = R(0);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) ga[q] = R(0);
+    if (colvalid && (pery || (kw >= 0 && kw < ny))) {
+        const size_t off = (size_t)kw * pitch + gx;
+        const TF* fr = fsrc + off;
+        const TG* gr = gsrc + off;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) fa[q] = (R)ld_st(fr + q * plane);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) ga[q] = (R)ld_st(gr + q * plane);
+        pa = ld_st(Psrc + off);
+    }
+
     for (int k = y0 - 3; k <= y1 + 3; ++k) {
+        const int bC = b0 >= 3 ? b0 - 3 : b0 + 2;   // slot5(k - 3)
+        const int bD = b0 >= 4 ? b0 - 4 : b0 + 1;   // slot5(k - 4)
         // ================= phase alpha =================
-        const bool doA = k < y1 + 3 && rowvalid(k);
-        R fa[9], ga[5], pa = R(0);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) fa[q] = R(0);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) ga[q] = R(0);
-        if (doA && colvalid) {
-            const size_t off = (size_t)grow(k) * pitch + gx;
-#pragma unroll
-            for (int q = 0; q < 9; ++q) fa[q] = (R)ld_st(fsrc + q * plane + off);
-#pragma unroll
-            for (int q = 0; q < 5; ++q) ga[q] = (R)ld_st(gsrc + q * plane + off);
-            pa = ld_st(Psrc + off);
-        }
+        const bool doA = k < y1 + 3 && (pery || (k >= 0 && k < ny));
 
         // ---- C(k-3): div u, grad T, Q, S and the D2Q5 MRT collision (Eq. 39)
         {
             const int r = k - 3;
-            if (r >= y0 - 1 && r < y1 + 1 && rowvalid(r) && inC) {
-                const int so = slot5(r);
-                R gd[5];
-#pragma unroll
-                for (int q = 0; q < 5; ++q) gd[q] = S.own[so][q][t];
-                const R rho = S.own[so][5][t];
-                const R Pp = S.own[so][6][t];
-                const R Td = gd[0] + gd[1] + gd[2] + gd[3] + gd[4];
-                const R T = Td + T_ref;
-                const R m1 = gd[1] - gd[3];
-                const R m2 = gd[2] - gd[4];
-                const R m3d = gd[1] + gd[2] + gd[3] + gd[4];
-                const R m4 = gd[1] - gd[2] + gd[3] - gd[4];
+            if (r >= y0 - 1 && r < y1 + 1 && (pery || (r >= 0 && r < ny)) && inC) {
+                const R4 o0 = S.own[bC][0][t];
+                const R4 o1 = S.own[bC][1][t];
+                const R g0 = o0.x, g1 = o0.y, g2 = o0.z, g3 = o0.w, g4 = o1.x;
+                const R rho = o1.y, Pp = o1.z, TdpdT = o1.w;
+                const R Td = ((g0 + g1) + (g2 + g3)) + g4;
+                const R m1 = g1 - g3;
+                const R m2 = g2 - g4;
+                const R m3d = (g1 + g3) + (g2 + g4);
+                const R m4 = (g1 + g3) - (g2 + g4);
                 // Eqs. 49-50: c_s^2 d_x T = -varsigma_1 m_1^(1), m_1^eq = 0
                 const R dTx = -P.vs1_cs2h * m1;
                 const R dTy = -P.vs1_cs2h * m2;
-                const int sc = slot3(r), sd = slot3(r - 1), su = slot3(r + 1);
-                const R uxc = S.ux[sc][t], uyc = S.uy[sc][t];
                 // neighbour rows: solid -> u = 0, open -> the boundary row
-                R uxS0, uxS1, uxS2, uyS0, uyS1, uyS2, uxN0, uxN1, uxN2, uyN0, uyN1, uyN2;
-                if (rowvalid(r - 1) || !wallS) {
-                    const int s = rowvalid(r - 1) ? sd : sc;
-                    uxS0 = S.ux[s][xl1]; uxS1 = S.ux[s][t]; uxS2 = S.ux[s][xr1];
-                    uyS0 = S.uy[s][xl1]; uyS1 = S.uy[s][t]; uyS2 = S.uy[s][xr1];
+                const bool vd = pery || r - 1 >= 0, vu = pery || r + 1 < ny;
+                const R2 uc = S.u[a0][t];
+                const R2 uW = S.u[a0][xl1], uE = S.u[a0][xr1];
+                R2 uS0, uS1, uS2, uN0, uN1, uN2;
+                if (vd || !wallS) {
+                    const int s = vd ? a1 : a0;
+                    uS0 = S.u[s][xl1]; uS1 = S.u[s][t]; uS2 = S.u[s][xr1];
                 } else {
-                    uxS0 = uxS1 = uxS2 = uyS0 = uyS1 = uyS2 = R(0);
+                    uS0.x = uS0.y = uS1.x = uS1.y = uS2.x = uS2.y = R(0);
                 }
-                if (rowvalid(r + 1) || !wallN) {
-                    const int s = rowvalid(r + 1) ? su : sc;
-                    uxN0 = S.ux[s][xl1]; uxN1 = S.ux[s][t]; uxN2 = S.ux[s][xr1];
-                    uyN0 = S.uy[s][xl1]; uyN1 = S.uy[s][t]; uyN2 = S.uy[s][xr1];
+                if (vu || !wallN) {
+                    const int s = vu ? a2 : a0;
+                    uN0 = S.u[s][xl1]; uN1 = S.u[s][t]; uN2 = S.u[s][xr1];
                 } else {
-                    uxN0 = uxN1 = uxN2 = uyN0 = uyN1 = uyN2 = R(0);
+                    uN0.x = uN0.y = uN1.x = uN1.y = uN2.x = uN2.y = R(0);
                 }
-                const R uxW = S.ux[sc][xl1], uxE = S.ux[sc][xr1];
-                const R uyW = S.uy[sc][xl1], uyE = S.uy[sc][xr1];
-                (void)uyW; (void)uyE; (void)uxS1; (void)uxN1;
                 // isotropic central difference, (1/c_s^2) sum_i w_i c_i phi(x + c_i)
-                const R divu = (uxE - uxW) * R(1.0 / 3.0) +
-                               (uxN2 + uxS2 - uxN0 - uxS0) * R(1.0 / 12.0) +
-                               (uyN1 - uyS1) * R(1.0 / 3.0) +
-                               (uyN2 + uyN0 - uyS2 - uyS0) * R(1.0 / 12.0);
+                const R divu = (uE.x - uW.x + uN1.y - uS1.y) * R(1.0 / 3.0) +
+                               ((uN2.x + uS2.x - uN0.x - uS0.x) +
+                                (uN2.y + uN0.y - uS2.y - uS0.y)) * R(1.0 / 12.0);
                 const R C = rho * P.cv;
                 // Q = -[rho c_v u.grad T + T (dp/dT)_rho div u]  (Eq. 20)
-                const R Q = -(C * (uxc * dTx + uyc * dTy) + T * eos_dpdT(P, rho, T) * divu);
-                const R Pn = Q / C;
-                // S = w^ rho c_v (dt/2) d_t^2 T with d_t^2 T ~ P^n - P^{n-1} (Eq. 24)
-                const R St = first ? R(0) : C * R(0.5) * (Pn - Pp);
-                const R Qs = Q + St;
+                const R Q = -(C * (uc.x * dTx + uc.y * dTy) + TdpdT * divu);
+                // P^n = Q / (rho c_v); S = w^ rho c_v (dt/2) d_t^2 T with
+                // d_t^2 T ~ P^n - P^{n-1} (Eq. 24), i.e. (Q - rho c_v P^{n-1}) / 2
+                const R Pn = Q * f_rcp(rho) * P.inv_cv;
+                const R Qs = first ? Q : Q + R(0.5) * (Q - C * Pp);
                 // moment-space collision (Eqs. 39, 40, 47), deviation form
                 const R m0s = Td + Qs;
-                const R m1s = P.one_m_vs1 * m1;
-                const R m2s = P.one_m_vs1 * m2;
                 const R m3s = m3d - P.vs3 * (m3d - P.w_dot * Td) + P.w_dot * Qs;
                 const R m4s = P.one_m_vs4 * m4;
+                const R h1 = R(0.5) * P.one_m_vs1 * m1, h2 = R(0.5) * P.one_m_vs1 * m2;
                 const R a = R(0.25) * (m3s + m4s), b = R(0.25) * (m3s - m4s);
-                S.gs[sc][0][t] = m0s - m3s;
-                S.gs[sc][1][t] = a + R(0.5) * m1s;
-                S.gs[sc][2][t] = b + R(0.5) * m2s;
-                S.gs[sc][3][t] = a - R(0.5) * m1s;
-                S.gs[sc][4][t] = b - R(0.5) * m2s;
-                if (inD && r >= y0 && r < y1) Pdst[(size_t)grow(r) * pitch + gx] = Pn;
+                S.gs[a0][0][t] = m0s - m3s;
+                S.gs[a0][1][t] = a + h1;
+                S.gs[a0][2][t] = b + h2;
+                S.gs[a0][3][t] = a - h1;
+                S.gs[a0][4][t] = b - h2;
+                if (inD && r >= y0 && r < y1) Pdst[(size_t)r * pitch + gx] = Pn;
             }
         }
 
@@ -196,156 +250,178 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
         {
             const int r = k - 3;
             if (r >= y0 && r < y1 && inD) {
-                const int sc = slot3(r), sd = slot3(r - 1), su = slot3(r + 1);
-                const bool vd = rowvalid(r - 1), vu = rowvalid(r + 1);
-                const int rowS = vd ? sd : sc;   // source row for c_y = +1 (open: own row)
-                const int rowN = vu ? su : sc;   // source row for c_y = -1
+                const bool vd = pery || r - 1 >= 0, vu = pery || r + 1 < ny;
+                const int rowS = vd ? a1 : a0;   // source row for c_y = +1 (open: own row)
+                const int rowN = vu ? a2 : a0;   // source row for c_y = -1
                 const bool bS = !vd && wallS, bN = !vu && wallN;
                 R fo[9];
                 if (P.frozen_flow) {
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) fo[q] = S.fs[sc][q][t];
+                    for (int q = 0; q < 9; ++q) fo[q] = S.fs[a0][q][t];
                 } else {
-                    fo[0] = S.fs[sc][0][t];
-                    fo[1] = S.fs[sc][1][xl1];
-                    fo[3] = S.fs[sc][3][xr1];
-                    fo[2] = bS ? S.fs[sc][4][t] : S.fs[rowS][2][t];
-                    fo[5] = bS ? S.fs[sc][7][t] : S.fs[rowS][5][xl1];
-                    fo[6] = bS ? S.fs[sc][8][t] : S.fs[rowS][6][xr1];
-                    fo[4] = bN ? S.fs[sc][2][t] : S.fs[rowN][4][t];
-                    fo[7] = bN ? S.fs[sc][5][t] : S.fs[rowN][7][xr1];
-                    fo[8] = bN ? S.fs[sc][6][t] : S.fs[rowN][8][xl1];
+                    fo[0] = S.fs[a0][0][t];
+                    fo[1] = S.fs[a0][1][xl1];
+                    fo[3] = S.fs[a0][3][xr1];
+                    fo[2] = bS ? S.fs[a0][4][t] : S.fs[rowS][2][t];
+                    fo[5] = bS ? S.fs[a0][7][t] : S.fs[rowS][5][xl1];
+                    fo[6] = bS ? S.fs[a0][8][t] : S.fs[rowS][6][xr1];
+                    fo[4] = bN ? S.fs[a0][2][t] : S.fs[rowN][4][t];
+                    fo[7] = bN ? S.fs[a0][5][t] : S.fs[rowN][7][xr1];
+                    fo[8] = bN ? S.fs[a0][6][t] : S.fs[rowN][8][xl1];
                 }
-                const size_t off = (size_t)grow(r) * pitch + gx;
+                TF* fw = fdst + (size_t)r * pitch + gx;
 #pragma unroll
-                for (int q = 0; q < 9; ++q) st_st(fdst + q * plane + off, (TF)fo[q]);
+                for (int q = 0; q < 9; ++q) st_st(fw + q * plane, (TF)fo[q]);
             }
         }
 
         // ---- A(k): moments, EOS, psi
-        R rho_a = R(1), rhod_a = R(0), jx_a = R(0), jy_a = R(0), T_a = R(0), psi_a = R(0);
+        R rho_a = R(1), rhod_a = R(0), jx_a = R(0), jy_a = R(0), psi_a = R(0), ir_a = R(1);
         if (doA && colvalid) {
             rhod_a = ((fa[0] + fa[1]) + (fa[2] + fa[3])) + ((fa[4] + fa[5]) + (fa[6] + fa[7])) + fa[8];
             rho_a = rhod_a + rho_ref;
-            const R Td = (ga[0] + ga[1]) + (ga[2] + ga[3]) + ga[4];
-            T_a = Td + T_ref;
+            ir_a = f_rcp(rho_a);
+            const R Td = ((ga[0] + ga[1]) + (ga[2] + ga[3])) + ga[4];
+            const R T_a = Td + T_ref;
             jx_a = (fa[1] - fa[3]) + (fa[5] - fa[6]) + (fa[8] - fa[7]);
             jy_a = (fa[2] - fa[4]) + (fa[5] + fa[6]) - (fa[7] + fa[8]);
-            const R q2 = psi2_of(P, rho_a, T_a);
+            R q2, TdpdT;
+            eos_node(P, rho_a, T_a, &q2, &TdpdT);
             if (!(q2 >= R(0))) errbits |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
-            psi_a = rsq(q2);
-            const int s3 = slot3(k), s5 = slot5(k);
-            S.psi[s3][t] = psi_a;
-            S.rho[s3][t] = rho_a;
-            S.T[s3][t] = T_a;
-#pragma unroll
-            for (int q = 0; q < 5; ++q) S.own[s5][q][t] = ga[q];
-            S.own[s5][5][t] = rho_a;
-            S.own[s5][6][t] = pa;
-            if (use_mass && inD && k >= y0 && k < y1) mass_acc += (double)rho_a;
+            psi_a = f_sqrt(q2);
+            S.psi[a0][t] = psi_a;
+            S.rho[a0][t] = rho_a;
+            S.T[a0][t] = T_a;
+            R4 o0, o1;
+            o0.x = ga[0]; o0.y = ga[1]; o0.z = ga[2]; o0.w = ga[3];
+            o1.x = ga[4]; o1.y = rho_a; o1.z = pa; o1.w = TdpdT;
+            S.own[b0][0][t] = o0;
+            S.own[b0][1][t] = o1;
+            mass_acc += (inD && k >= y0 && k < y1) ? rho_a : R(0);
         }
         __syncthreads();
 
         // ================= phase beta =================
+        // keep row k's populations for B(k) and issue the loads of row k + 1
+        R fpn[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) fpn[q] = fa[q];
+        {
+            const int kn = k + 1;
+            const int kwn = (pery && kw == ny - 1) ? 0 : kw + 1;
+            if (kn < y1 + 3 && (pery || (kn >= 0 && kn < ny)) && colvalid) {
+                const size_t off = (size_t)kwn * pitch + gx;
+                const TF* fr = fsrc + off;
+                const TG* gr = gsrc + off;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) fa[q] = (R)ld_st(fr + q * plane);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) ga[q] = (R)ld_st(gr + q * plane);
+                pa = ld_st(Psrc + off);
+            }
+        }
         // ---- B(k-1): interaction force, velocity, D2Q9 MRT collision
         {
             const int r = k - 1;
-            if (r >= y0 - 2 && r < y1 + 2 && rowvalid(r) && inB) {
-                const int sc = slot3(r), sd = slot3(r - 1), su = slot3(r + 1);
-                const bool vd = rowvalid(r - 1), vu = rowvalid(r + 1);
+            if (r >= y0 - 2 && r < y1 + 2 && (pery || (r >= 0 && r < ny)) && inB) {
+                const bool vd = pery || r - 1 >= 0, vu = pery || r + 1 < ny;
                 R pSW, pS, pSE, pNW, pN, pNE;
-                const R pW = S.psi[sc][xl1], pE = S.psi[sc][xr1];
-                // Ding-Spelt ghost layer (Section 3.3): rho_ghost = rho(layer 2)
-                // + tan(pi/2 - theta) |rho(x+1, layer 1) - rho(x-1, layer 1)|
-                auto ghost = [&](int c, int cm, int cp, int s_far, int edge) -> R {
-                    const R rg = S.rho[s_far][c] + cot * rabs(S.rho[sc][cp] - S.rho[sc][cm]);
-                    const R Tg = I.therm[edge] == T_DIRICHLET ? (R)wall_T(I, edge, gcol(c))
-                                                              : S.T[sc][c];
-                    const R q2 = psi2_of(P, rg, Tg);
-                    if (!(q2 >= R(0))) errbits |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
-                    return rsq(q2);
-                };
+                const R pW = S.psi[a1][xl1], pE = S.psi[a1][xr1];
                 if (vd || !wallS) {
-                    const int s = vd ? sd : sc;
+                    const int s = vd ? a2 : a1;
                     pSW = S.psi[s][xl1]; pS = S.psi[s][t]; pSE = S.psi[s][xr1];
                 } else {
-                    pSW = ghost(xl1, cLL, cLR, su, ES);
-                    pS = ghost(t, xl1, xr1, su, ES);
-                    pSE = ghost(xr1, cRL, cRR, su, ES);
+                    // south wall: layer 1 = row r (a1), layer 2 = row r + 1 (a0)
+                    const bool dr = I.therm[ES] == T_DIRICHLET;
+                    pSW = ghost_psi(P, S.rho[a0][xl1], S.rho[a1][cLR], S.rho[a1][cLL], cot,
+                                    dr ? TgS_l : S.T[a1][xl1], &errbits);
+                    pS = ghost_psi(P, S.rho[a0][t], S.rho[a1][xr1], S.rho[a1][xl1], cot,
+                                   dr ? TgS_c : S.T[a1][t], &errbits);
+                    pSE = ghost_psi(P, S.rho[a0][xr1], S.rho[a1][cRR], S.rho[a1][cRL], cot,
+                                    dr ? TgS_r : S.T[a1][xr1], &errbits);
                 }
                 if (vu || !wallN) {
-                    const int s = vu ? su : sc;
+                    const int s = vu ? a0 : a1;
                     pNW = S.psi[s][xl1]; pN = S.psi[s][t]; pNE = S.psi[s][xr1];
                 } else {
-                    pNW = ghost(xl1, cLL, cLR, sd, EN);
-                    pN = ghost(t, xl1, xr1, sd, EN);
-                    pNE = ghost(xr1, cRL, cRR, sd, EN);
+                    // north wall: layer 1 = row r (a1), layer 2 = row r - 1 (a2)
+                    const bool dr = I.therm[EN] == T_DIRICHLET;
+                    pNW = ghost_psi(P, S.rho[a2][xl1], S.rho[a1][cLR], S.rho[a1][cLL], cot,
+                                    dr ? TgN : S.T[a1][xl1], &errbits);
+                    pN = ghost_psi(P, S.rho[a2][t], S.rho[a1][xr1], S.rho[a1][xl1], cot,
+                                   dr ? TgN : S.T[a1][t], &errbits);
+                    pNE = ghost_psi(P, S.rho[a2][xr1], S.rho[a1][cRR], S.rho[a1][cRL], cot,
+                                    dr ? TgN : S.T[a1][xr1], &errbits);
                 }
                 // Eq. 9 with varpi(1) = 1/3, varpi(2) = 1/12
-                const R sx = (pE - pW) * R(1.0 / 3.0) + (pNE + pSE - pNW - pSW) * R(1.0 / 12.0);
-                const R sy = (pN - pS) * R(1.0 / 3.0) + (pNE + pNW - pSE - pSW) * R(1.0 / 12.0);
+                const R sx = (pE - pW) * R(1.0 / 3.0) + ((pNE - pSW) + (pSE - pNW)) * R(1.0 / 12.0);
+                const R sy = (pN - pS) * R(1.0 / 3.0) + ((pNE - pSW) + (pNW - pSE)) * R(1.0 / 12.0);
                 const R Fmx = P.negG * psip * sx;
                 const R Fmy = P.negG * psip * sy;
                 const R Fx = Fmx;
                 const R Fy = Fmy - P.gravity * (rhop - rho_ave);
                 R ux = R(0), uy = R(0);
                 if (!P.frozen_flow) {
-                    const R ir = R(1) / rhop;
-                    ux = (jxp + R(0.5) * Fx) * ir;
-                    uy = (jyp + R(0.5) * Fy) * ir;
+                    ux = (jxp + R(0.5) * Fx) * irp;
+                    uy = (jyp + R(0.5) * Fy) * irp;
                 }
-                S.ux[sc][t] = ux;
-                S.uy[sc][t] = uy;
+                R2 uv;
+                uv.x = ux;
+                uv.y = uy;
+                S.u[a1][t] = uv;
                 if (r >= y0 - 1 && r < y1 + 1 && inC) {
+                    R* fsw = &S.fs[a1][0][t];
                     if (P.frozen_flow) {
 #pragma unroll
-                        for (int q = 0; q < 9; ++q) S.fs[sc][q][t] = fp[q];
+                        for (int q = 0; q < 9; ++q) fsw[q * NT] = fp[q];
                     } else {
                         const R* f = fp;
                         const R rr = rhop;
-                        const R uu = ux * ux + uy * uy;
-                        const R s14 = (f[1] + f[2]) + (f[3] + f[4]);
-                        const R s58 = (f[5] + f[6]) + (f[7] + f[8]);
+                        const R rux = rr * ux, ruy = rr * uy;
+                        const R ruu = rux * ux + ruy * uy;
+                        const R s14 = (f[1] + f[3]) + (f[2] + f[4]);
+                        const R s58 = (f[5] + f[7]) + (f[6] + f[8]);
                         // non-equilibrium parts m - m^eq of the moments of Eq. 7
                         // (deviation storage shifts m_e by -2 rho_ref, m_eps by rho_ref)
-                        const R ne1 = (R(-4) * f[0] - s14 + R(2) * s58) + R(2) * rhodp - R(3) * rr * uu;
-                        const R ne2 = (R(4) * f[0] - R(2) * s14 + s58) - rhodp + R(3) * rr * uu;
-                        const R ne4 = (R(-2) * f[1] + R(2) * f[3] + f[5] - f[6] - f[7] + f[8]) + rr * ux;
-                        const R ne6 = (R(-2) * f[2] + R(2) * f[4] + f[5] + f[6] - f[7] - f[8]) + rr * uy;
-                        const R ne7 = (f[1] - f[2] + f[3] - f[4]) - rr * (ux * ux - uy * uy);
-                        const R ne8 = (f[5] - f[6] + f[7] - f[8]) - rr * ux * uy;
-                        // Li forcing (Eq. 8)
+                        const R ne1 = R(2) * (s58 + rhodp - f[0]) - (R(2) * f[0] + s14) - R(3) * ruu;
+                        const R ne2 = (R(4) * f[0] - R(2) * s14 + s58) - rhodp + R(3) * ruu;
+                        const R d13 = f[1] - f[3], d24 = f[2] - f[4];
+                        const R d58 = f[5] - f[7], d68 = f[6] - f[8];
+                        const R ne4 = (d58 - d68 - R(2) * d13) + rux;
+                        const R ne6 = (d58 + d68 - R(2) * d24) + ruy;
+                        const R ne7 = (f[1] + f[3]) - (f[2] + f[4]) - (rux * ux - ruy * uy);
+                        const R ne8 = (f[5] + f[7]) - (f[6] + f[8]) - rux * uy;
+                        // Li forcing (Eq. 8); |F_m|^2 / psi^2 = G^2 |sum varpi psi c|^2
                         const R uF = ux * Fx + uy * Fy;
-                        const R Fm2 = (Fmx * Fmx + Fmy * Fmy) / (psip * psip);
+                        const R Fm2 = P.negG * P.negG * (sx * sx + sy * sy);
                         const R F1 = R(6) * uF + P.sig_e * Fm2;
                         const R F2 = R(-6) * uF - P.sig_eps * Fm2;
                         const R F7 = R(2) * (ux * Fx - uy * Fy);
                         const R F8 = ux * Fy + uy * Fx;
                         // m* - m = -S (m - m^eq) + (I - S/2) F; for j the
                         // change is exactly F because rho u = j + F/2
-                        const R d1 = -P.s_e * ne1 + P.hs_e * F1;
-                        const R d2 = -P.s_eps * ne2 + P.hs_eps * F2;
-                        const R d4 = -P.s_q * ne4 - P.hs_q * Fx;
-                        const R d6 = -P.s_q * ne6 - P.hs_q * Fy;
-                        const R d7 = -P.s_p * ne7 + P.hs_p * F7;
-                        const R d8 = -P.s_p * ne8 + P.hs_p * F8;
+                        const R a1m = (P.hs_e * F1 - P.s_e * ne1) * R(1.0 / 36.0);
+                        const R a2m = (P.hs_eps * F2 - P.s_eps * ne2) * R(1.0 / 36.0);
+                        const R a3 = Fx * R(1.0 / 6.0), a5 = Fy * R(1.0 / 6.0);
+                        const R a4 = -(P.s_q * ne4 + P.hs_q * Fx) * R(1.0 / 12.0);
+                        const R a6 = -(P.s_q * ne6 + P.hs_q * Fy) * R(1.0 / 12.0);
+                        const R a7 = (P.hs_p * F7 - P.s_p * ne7) * R(0.25);
+                        const R a8 = (P.hs_p * F8 - P.s_p * ne8) * R(0.25);
                         // f* = f + M^{-1} (m* - m), M^{-1} = M^T diag(1/9, 1/36,
                         // 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-                        const R a1 = d1 * R(1.0 / 36.0), a2 = d2 * R(1.0 / 36.0);
-                        const R a3 = Fx * R(1.0 / 6.0), a5 = Fy * R(1.0 / 6.0);
-                        const R a4 = d4 * R(1.0 / 12.0), a6 = d6 * R(1.0 / 12.0);
-                        const R a7 = d7 * R(0.25), a8 = d8 * R(0.25);
-                        const R cax = -a1 - R(2) * a2;   // common to the axis directions
-                        const R cdg = R(2) * a1 + a2;    // common to the diagonals
-                        S.fs[sc][0][t] = f[0] - R(4) * a1 + R(4) * a2;
-                        S.fs[sc][1][t] = f[1] + cax + a3 - R(2) * a4 + a7;
-                        S.fs[sc][2][t] = f[2] + cax + a5 - R(2) * a6 - a7;
-                        S.fs[sc][3][t] = f[3] + cax - a3 + R(2) * a4 + a7;
-                        S.fs[sc][4][t] = f[4] + cax - a5 + R(2) * a6 - a7;
-                        S.fs[sc][5][t] = f[5] + cdg + a3 + a4 + a5 + a6 + a8;
-                        S.fs[sc][6][t] = f[6] + cdg - a3 - a4 + a5 + a6 - a8;
-                        S.fs[sc][7][t] = f[7] + cdg - a3 - a4 - a5 - a6 + a8;
-                        S.fs[sc][8][t] = f[8] + cdg + a3 + a4 - a5 - a6 - a8;
+                        const R cax = -a1m - R(2) * a2m;   // common to the axis directions
+                        const R cdg = R(2) * a1m + a2m;    // common to the diagonals
+                        const R ex = a3 - R(2) * a4, ey = a5 - R(2) * a6;
+                        const R dx = a3 + a4, dy = a5 + a6;
+                        fsw[0 * NT] = f[0] + R(4) * (a2m - a1m);
+                        fsw[1 * NT] = f[1] + cax + ex + a7;
+                        fsw[2 * NT] = f[2] + cax + ey - a7;
+                        fsw[3 * NT] = f[3] + cax - ex + a7;
+                        fsw[4 * NT] = f[4] + cax - ey - a7;
+                        fsw[5 * NT] = f[5] + cdg + dx + dy + a8;
+                        fsw[6 * NT] = f[6] + cdg - dx + dy - a8;
+                        fsw[7 * NT] = f[7] + cdg - dx - dy + a8;
+                        fsw[8 * NT] = f[8] + cdg + dx - dy - a8;
                     }
                 }
             }
@@ -355,59 +431,64 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
         {
             const int r = k - 4;
             if (r >= y0 && r < y1 && inD) {
-                const int so = slot5(r);
-                const int sc = slot3(r), sd = slot3(r - 1), su = slot3(r + 1);
-                R gd[5];
-#pragma unroll
-                for (int q = 0; q < 5; ++q) gd[q] = S.own[so][q][t];
+                const R4 o0 = S.own[bD][0][t];
+                const R4 o1 = S.own[bD][1][t];
                 R go[5];
                 if (P.frozen_thermal) {
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) go[q] = gd[q];
+                    go[0] = o0.x; go[1] = o0.y; go[2] = o0.z; go[3] = o0.w; go[4] = o1.x;
                 } else {
-                    const R rho = S.own[so][5][t];
+                    const bool vd = pery || r - 1 >= 0, vu = pery || r + 1 < ny;
+                    const R* gsc = &S.gs[a1][0][t];
                     // thermal walls: halfway anti-bounce-back (Dirichlet) or
                     // bounce-back (adiabatic) supplies the incoming g*
-                    auto wallg = [&](int edge, int opp) -> R {
-                        const R out = S.gs[sc][opp][t];
-                        if (I.therm[edge] == T_DIRICHLET)
-                            return -out + R(2) * P.w5_1 * ((R)wall_T(I, edge, gx) - T_ref);
-                        return out;
-                    };
-                    R A[5];
-                    A[0] = S.gs[sc][0][t];
-                    A[1] = left_edge ? wallg(EW, 3) : S.gs[sc][1][xl1];
-                    A[3] = right_edge ? wallg(EE, 1) : S.gs[sc][3][xr1];
-                    A[2] = rowvalid(r - 1) ? S.gs[sd][2][t] : wallg(ES, 4);
-                    A[4] = rowvalid(r + 1) ? S.gs[su][4][t] : wallg(EN, 2);
-                    const R iC = R(1) / (rho * P.cv);
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) go[q] = gd[q] + (A[q] - gd[q]) * iC;
+                    R A1, A2, A3, A4;
+                    if (left_edge) A1 = dirW ? twW2 - gsc[3 * NT] : gsc[3 * NT];
+                    else A1 = S.gs[a1][1][xl1];
+                    if (right_edge) A3 = dirE ? twE2 - gsc[1 * NT] : gsc[1 * NT];
+                    else A3 = S.gs[a1][3][xr1];
+                    if (vd) A2 = S.gs[a2][2][t];
+                    else A2 = dirS ? twS2 - gsc[4 * NT] : gsc[4 * NT];
+                    if (vu) A4 = S.gs[a0][4][t];
+                    else A4 = dirN ? twN2 - gsc[2 * NT] : gsc[2 * NT];
+                    const R A0 = gsc[0];
+                    const R iC = f_rcp(o1.y * P.cv);
+                    go[0] = o0.x + (A0 - o0.x) * iC;
+                    go[1] = o0.y + (A1 - o0.y) * iC;
+                    go[2] = o0.z + (A2 - o0.z) * iC;
+                    go[3] = o0.w + (A3 - o0.w) * iC;
+                    go[4] = o1.x + (A4 - o1.x) * iC;
                 }
-                const size_t off = (size_t)grow(r) * pitch + gx;
+                TG* gw = gdst + (size_t)r * pitch + gx;
 #pragma unroll
-                for (int q = 0; q < 5; ++q) st_st(gdst + q * plane + off, go[q]);
+                for (int q = 0; q < 5; ++q) st_st(gw + q * plane, go[q]);
             }
         }
         __syncthreads();
 
 #pragma unroll
-        for (int q = 0; q < 9; ++q) fp[q] = fa[q];
+        for (int q = 0; q < 9; ++q) fp[q] = fpn[q];
         rhop = rho_a;
         rhodp = rhod_a;
         jxp = jx_a;
         jyp = jy_a;
-        Tp = T_a;
         psip = psi_a;
+        irp = ir_a;
+        // rotate the ring slots and the wrapped load row
+        const int tmp = a2;
+        a2 = a1;
+        a1 = a0;
+        a0 = tmp;
+        b0 = b0 == 4 ? 0 : b0 + 1;
+        kw = (pery && kw == ny - 1) ? 0 : kw + 1;
     }
-    (void)Tp;
 
     if (errbits) atomicOr(&I.ctl->err, errbits);
     if (use_mass) {
         // block sum of this unit's output densities -> ring slot step % 3
+        double macc = (double)mass_acc;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mass_acc += __shfl_down_sync(0xffffffffu, mass_acc, o);
-        if ((t & 31) == 0) S.red[t >> 5] = mass_acc;
+        for (int o = 16; o > 0; o >>= 1) macc += __shfl_down_sync(0xffffffffu, macc, o);
+        if ((t & 31) == 0) S.red[t >> 5] = macc;
         __syncthreads();
         if (t == 0) {
             double s = 0.0;
@@ -419,7 +500,8 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
 }
 
 template <int PREC, int NT>
-__global__ void __launch_bounds__(NT) k_step(StepLaunch L, Phys<typename Types<PREC>::R> P) {
+__global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
+    k_step(StepLaunch L, Phys<typename Types<PREC>::R> P) {
     typedef typename Types<PREC>::R R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<R, NT>& S = *reinterpret_cast<StepSmem<R, NT>*>(smem_raw);
@@ -430,8 +512,7 @@ __global__ void __launch_bounds__(NT) k_step(StepLaunch L, Phys<typename Types<P
         __syncthreads();
         if (u >= L.n_units) break;
         const Unit U = L.units[u];
-        const Inst I = L.insts[U.inst];
-        process_unit<PREC, NT>(I, U, P, S);
+        process_unit<PREC, NT>(L.insts[U.inst], U, P, S);
     }
     if (threadIdx.x == 0) {
         __threadfence();
