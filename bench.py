@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-instances", type=int, default=512)
+    ap.add_argument("--serve-steps", type=int, default=500)
     ap.add_argument("--size", type=int, default=NX,
                     help="domain side (default 4096; smaller sides for profiler captures)")
     return ap.parse_args()
@@ -180,6 +183,43 @@ def accuracy_check():
             **{k: float("%.3e" % v) for k, v in out.items()}}
 
 
+def served_check(n_inst, steps, budget_gb=1.0):
+    """The batched + served population: n_inst open-evaporation domains with
+    sides uniform in 64..512, each advanced `steps` steps, arriving in a
+    seeded Poisson stream and admitted into a 1 GB device budget; reports
+    p50 / p99 time-to-N-steps and aggregate MLUPS, next to the same work run
+    one domain at a time through the single-domain path."""
+    import paper_2205_00686_gb300 as lbm
+    from paper_2205_00686_gb300 import workloads as W
+    from paper_2205_00686_gb300.serve import CudaBackend, Server
+    cases = W.batch_instances(n_inst, steps=steps)
+    gaps = -np.log(1.0 - W.uniform(77, n_inst)) * 0.002       # mean 2 ms between arrivals
+    arrivals = [(float(t), c, steps) for t, c in zip(np.cumsum(gaps), cases)]
+    be = CudaBackend("fp32")
+    srv = Server(be, mem_budget=int(budget_gb * 2 ** 30), chunk=100)
+    st = srv.run(arrivals)
+    nodes = sum(c.nx * c.ny for c in cases)
+    # the same requests one at a time through lbm_step (first 32 of them)
+    import torch
+    m = min(32, n_inst)
+    t0 = time.perf_counter()
+    for c in cases[:m]:
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+        d.init_fields(*c.fields())
+        d.step(steps)
+        d.get_rho_u_T()
+        d.close()
+    torch.cuda.synchronize()
+    t_solo = time.perf_counter() - t0
+    solo_mlups = sum(c.nx * c.ny for c in cases[:m]) * steps / t_solo / 1e6
+    return {"instances": n_inst, "steps_each": steps, "total_nodes": nodes,
+            "budget_gb": budget_gb, "mlups": round(st["mlups"], 1),
+            "p50_s": round(st["p50_s"], 4), "p99_s": round(st["p99_s"], 4),
+            "wall_s": round(st["wall_s"], 2), "failed": st["failed"],
+            "max_concurrent": st["max_active"],
+            "sequential_single_domain_mlups": round(solo_mlups, 1)}
+
+
 def time_device(dom, steps, warmup, stream, torch, dist, world):
     dom.step(warmup)
     dom.sync()
@@ -294,6 +334,8 @@ def run_ours(args):
                               "hbm_frac_of_measured": round(BYTES_PER_NODE["fp32_g16"] * N / (tg / args.steps) / 1e9 / peak, 4)}
         dg.close()
         extras["error_vs_oracle"] = accuracy_check()
+        if not args.no_serve:
+            extras["served"] = served_check(args.serve_instances, args.serve_steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1,0 +1,235 @@
+"""Continuous-batching request loop for many independent simulations.
+
+A request is one simulation (a `workloads.Case`-like object: sizes, params,
+boundary spec, initial fields) to be advanced by a number of steps.  The
+server
+
+* admits waiting requests while their device memory fits the budget (each
+  domain's state lives in a PyTorch-allocated device buffer handed to
+  `lbm_create`, so the budget is real memory, and is returned to PyTorch's
+  caching allocator when the request retires);
+* keeps every admitted domain resident and advances all of them together
+  with `lbm_batch_step`: one persistent kernel launch per step walks the
+  work units of every domain, so requests that arrived at different times
+  overlap on the GPU;
+* between chunks of steps, retires the domains that reached their target,
+  copies their fields to the host, frees their memory and admits new
+  requests into the freed space (continuous batching: no request waits for
+  the whole batch to finish);
+* records, per request, the time from arrival to completion, and overall
+  the aggregate node updates per second.
+
+Requests in one batch must share precision and physical parameters (the
+library's batch rule); the server keeps one batch per distinct parameter
+set.  All numerics run in the CUDA library; this module only schedules.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    case: object            # nx, ny, params, bc, fields()
+    steps: int
+    arrival: float = 0.0
+    admitted: Optional[float] = None
+    finished: Optional[float] = None
+    result: Optional[tuple] = None      # (rho, ux, uy, T) host arrays
+    error: int = 0
+    done_steps: int = 0
+
+    @property
+    def latency(self) -> Optional[float]:
+        return None if self.finished is None else self.finished - self.arrival
+
+
+class CudaBackend:
+    """The real engine: PyTorch device buffers + the library's C ABI."""
+
+    def __init__(self, prec: str = "fp32", stream=None):
+        import torch
+
+        import paper_2205_00686_gb300 as lbm
+        self.torch = torch
+        self.lbm = lbm
+        self.prec = prec
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.batches: Dict[tuple, object] = {}
+        self.handles: Dict[int, tuple] = {}
+
+    def bytes_for(self, case) -> int:
+        # state (both ping-pong copies) plus the field buffers read at retirement
+        return self.lbm.lbm_state_bytes(case.nx, case.ny, self.prec) + 32 * case.nx * case.ny
+
+    def _key(self, case):
+        return tuple(sorted((k, float(v)) for k, v in case.params.items()))
+
+    def open(self, case):
+        torch = self.torch
+        nbytes = self.lbm.lbm_state_bytes(case.nx, case.ny, self.prec)
+        buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        d = self.lbm.Domain(case.nx, case.ny, case.params, case.bc, prec=self.prec,
+                            stream=self.stream.cuda_stream, device_mem=buf.data_ptr(),
+                            device_bytes=nbytes)
+        d.init_fields(*case.fields())
+        key = self._key(case)
+        if key not in self.batches:
+            self.batches[key] = self.lbm.Batch(stream=self.stream.cuda_stream)
+        self.batches[key].attach(d)
+        h = (d, buf, key)
+        self.handles[id(h)] = h
+        return h
+
+    def step(self, n: int):
+        for b in self.batches.values():
+            if len(b):
+                b.step(n)
+
+    def sync(self) -> Dict[int, int]:
+        """Waits; returns {id(handle): error} for handles with a device error."""
+        failed = False
+        for b in self.batches.values():
+            if len(b) and b.sync() != 0:
+                failed = True
+        errs = {}
+        if failed:
+            for hid, h in self.handles.items():
+                try:
+                    h[0].sync()
+                except self.lbm.LbmError as e:
+                    errs[hid] = e.code
+        return errs
+
+    def close(self, handle, read: bool = True):
+        d, buf, key = handle
+        self.handles.pop(id(handle), None)
+        self.batches[key].detach(d)
+        out = None
+        if read:
+            out = d.get_rho_u_T()
+        d.close()
+        del buf
+        return out
+
+
+
+class Server:
+    """Admission by device memory + chunked continuous batching."""
+
+    def __init__(self, backend, mem_budget: int, chunk: int = 100,
+                 clock: Callable[[], float] = time.perf_counter):
+        self.backend = backend
+        self.mem_budget = int(mem_budget)
+        self.chunk = int(chunk)
+        self.clock = clock
+        self.waiting: collections.deque = collections.deque()
+        self.active: Dict[int, tuple] = {}       # rid -> (request, handle, bytes)
+        self.finished: List[Request] = []
+        self.mem_used = 0
+        self.node_updates = 0
+        self.t_start: Optional[float] = None
+        self.max_active = 0
+        self._next = 0
+
+    # ---- request side -------------------------------------------------------
+    def submit(self, case, steps: int, arrival: Optional[float] = None) -> Request:
+        if steps < 1:
+            raise ValueError("steps must be >= 1")
+        need = self.backend.bytes_for(case)
+        if need > self.mem_budget:
+            raise ValueError("request needs %d bytes, more than the whole budget" % need)
+        r = Request(self._next, case, int(steps), self.clock() if arrival is None else arrival)
+        self._next += 1
+        self.waiting.append(r)
+        return r
+
+    # ---- scheduling ---------------------------------------------------------
+    def _admit(self):
+        # first come, first served; a request that does not fit blocks the
+        # ones behind it (no starvation of large requests)
+        while self.waiting:
+            r = self.waiting[0]
+            need = self.backend.bytes_for(r.case)
+            if self.mem_used + need > self.mem_budget:
+                break
+            self.waiting.popleft()
+            h = self.backend.open(r.case)
+            r.admitted = self.clock()
+            self.active[r.rid] = (r, h, need)
+            self.mem_used += need
+            self.max_active = max(self.max_active, len(self.active))
+
+    def _retire(self, rid, error=0):
+        r, h, need = self.active.pop(rid)
+        r.result = self.backend.close(h, read=error == 0)
+        r.error = error
+        r.finished = self.clock()
+        self.mem_used -= need
+        self.finished.append(r)
+
+    def tick(self) -> bool:
+        """One scheduling round: admit, advance a chunk, retire.  Returns
+        False when there is nothing left to do."""
+        if self.t_start is None:
+            self.t_start = self.clock()
+        self._admit()
+        if not self.active:
+            return bool(self.waiting)
+        # every active domain advances together: the chunk ends at the
+        # earliest completion so that no domain overshoots its target
+        n = min(self.chunk, min(r.steps - r.done_steps for r, _, _ in self.active.values()))
+        self.backend.step(n)
+        errs = self.backend.sync()
+        for rid, (r, h, _) in list(self.active.items()):
+            r.done_steps += n
+            self.node_updates += n * r.case.nx * r.case.ny
+            e = errs.get(id(h))
+            if e:
+                self._retire(rid, error=e)
+            elif r.done_steps >= r.steps:
+                self._retire(rid)
+        return bool(self.active or self.waiting)
+
+    def run(self, arrivals=None):
+        """Runs until every request is done.  `arrivals` optionally lists
+        (time_offset_s, case, steps) submitted when the clock passes them
+        (requests arriving while others are on the GPU)."""
+        pending = collections.deque(sorted(arrivals or [], key=lambda a: a[0]))
+        t0 = self.clock()
+        if self.t_start is None:
+            self.t_start = t0
+        while True:
+            now = self.clock()
+            while pending and pending[0][0] <= now - t0:
+                off, case, steps = pending.popleft()
+                self.submit(case, steps, arrival=t0 + off)
+            busy = self.tick()
+            if not busy and not pending:
+                break
+            if not busy and pending:
+                # idle until the next arrival
+                wait = pending[0][0] - (self.clock() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+        return self.stats()
+
+    def stats(self) -> dict:
+        lat = np.array([r.latency for r in self.finished if r.latency is not None and not r.error])
+        wall = (self.clock() - self.t_start) if self.t_start is not None else 0.0
+        return {
+            "requests": len(self.finished),
+            "failed": sum(1 for r in self.finished if r.error),
+            "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "node_updates": int(self.node_updates),
+            "wall_s": wall,
+            "mlups": self.node_updates / wall / 1e6 if wall > 0 else None,
+            "max_active": self.max_active,
+        }

@@ -1,0 +1,153 @@
+"""Batched stepping (one persistent launch per step over a work list of
+(domain, strip, segment) units from many domains): every domain's result must
+be the one it gets alone."""
+import numpy as np
+import pytest
+
+import parity as P
+from paper_2205_00686_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def mixed_cases(gravity=0.0):
+    v = P.bc_variants()
+    specs = [(64, 64, "periodic"), (100, 80, "open_dirichlet"), (257, 129, "wall_open_heater"),
+             (33, 47, "two_walls_adiabatic"), (512, 64, "periodic_x_open_y"),
+             (130, 200, "open_x_walls_y"), (17, 13, "open_x_periodic_y")]
+    return [P.droplet_case(nx, ny, v[name], seed=11 + i, gravity=gravity)
+            for i, (nx, ny, name) in enumerate(specs)]
+
+
+def solo(case, steps, prec):
+    return P.run_gpu(case, steps, prec).populations()
+
+
+def test_batch_matches_solo_bitwise():
+    import paper_2205_00686_gb300 as lbm
+    cases = mixed_cases()
+    b = lbm.Batch()
+    doms = []
+    for c in cases:
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+        d.init_fields(*c.fields())
+        b.attach(d)
+        doms.append(d)
+    assert len(b) == len(cases)
+    b.step(60)
+    assert b.sync() == 0
+    for c, d in zip(cases, doms):
+        b.detach(d)
+        f, g, Pp = d.populations()
+        fs, gs, Ps = solo(c, 60, "fp32")
+        assert np.array_equal(f, fs) and np.array_equal(g, gs) and np.array_equal(Pp, Ps), c.name
+        assert d.step_count == 60
+    b.close()
+
+
+def test_attach_and_detach_mid_run():
+    """Domains join and leave between launches; each keeps its own step
+    counter, ping-pong parity and d_t^2 T history."""
+    import paper_2205_00686_gb300 as lbm
+    cases = mixed_cases()[:3]
+    b = lbm.Batch()
+    d = [lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32") for c in cases]
+    for x, c in zip(d, cases):
+        x.init_fields(*c.fields())
+    b.attach(d[0])
+    b.step(31)                  # d0 at 31 (odd parity)
+    b.attach(d[1])
+    b.step(20)                  # d0 51, d1 20
+    b.detach(d[0])
+    b.attach(d[2])
+    b.step(45)                  # d1 65, d2 45 (graph replay path)
+    b.detach(d[1])
+    b.detach(d[2])
+    d[0].step(9)                # continue alone: 60
+    for x, c, n in zip(d, cases, (60, 65, 45)):
+        f, g, _ = x.populations()
+        fs, gs, _ = solo(c, n, "fp32")
+        assert x.step_count == n
+        assert np.array_equal(f, fs) and np.array_equal(g, gs), c.name
+    b.close()
+
+
+def test_batch_fp64_with_gravity_matches_oracle():
+    """Each domain keeps its own buoyancy density history in the batch."""
+    import paper_2205_00686_gb300 as lbm
+    cases = mixed_cases(gravity=3e-5)[1:4]
+    b = lbm.Batch()
+    doms = []
+    for c in cases:
+        x = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp64")
+        x.init_fields(*c.fields())
+        b.attach(x)
+        doms.append(x)
+    b.step(40)
+    assert b.sync() == 0
+    for c, x in zip(cases, doms):
+        o = P.run_oracle(c, 40)
+        fe = P.field_errors(x.get_rho_u_T(), o.fields())
+        assert max(fe.values()) <= 1e-12, (c.name, fe)
+    b.close()
+
+
+def test_poisoned_domain_fails_alone():
+    """A domain that goes out of the EOS range flags only itself; after it
+    is detached the others continue exactly as they would alone."""
+    import paper_2205_00686_gb300 as lbm
+    cases = mixed_cases()[:4]
+    bad = 2
+    b = lbm.Batch()
+    doms = []
+    for i, c in enumerate(cases):
+        x = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+        rho = c.rho.copy()
+        if i == bad:
+            rho[c.ny // 2, c.nx // 2] = 9.7       # psi^2 < 0 there
+        x.init_fields(rho, c.ux, c.uy, c.T)
+        b.attach(x)
+        doms.append(x)
+    b.step(3)
+    assert b.sync() == lbm.LBM_EPSI
+    with pytest.raises(lbm.LbmError) as ei:
+        doms[bad].sync()
+    assert ei.value.code == lbm.LBM_EPSI
+    b.detach(doms[bad])
+    b.step(27)
+    assert b.sync() == 0
+    for i, (c, x) in enumerate(zip(cases, doms)):
+        if i == bad:
+            continue
+        assert x.sync() == 0
+        f, g, _ = x.populations()
+        fs, gs, _ = solo(c, 30, "fp32")
+        assert np.array_equal(f, fs) and np.array_equal(g, gs), c.name
+    b.close()
+
+
+def test_batch_rejects_mixed_physics():
+    import paper_2205_00686_gb300 as lbm
+    c = mixed_cases()[0]
+    b = lbm.Batch()
+    x = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+    x.init_fields(*c.fields())
+    y = lbm.Domain(c.nx, c.ny, W.params(lambda_=0.2), c.bc, prec="fp32")
+    y.init_fields(*c.fields())
+    z = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp64")
+    z.init_fields(*c.fields())
+    b.attach(x)
+    with pytest.raises(lbm.LbmError):
+        b.attach(y)
+    with pytest.raises(lbm.LbmError):
+        b.attach(z)
+    with pytest.raises(lbm.LbmError) as ei:
+        x.step(1)                 # attached: the batch owns its stepping
+    assert ei.value.code == lbm.LBM_ESTATE
+    b.close()
