@@ -46,7 +46,7 @@ struct Vec4;
 template <>
 struct Vec4<float> { typedef float4 T; };
 template <>
-struct Vec4<double> { typedef double4 T; };
+struct Vec4<double> { typedef double4_32a T; };
 
 template <class R, int NT>
 struct StepSmem {
@@ -73,124 +73,180 @@ __device__ __forceinline__ R ghost_psi(const Phys<R>& P, R rho_far, R rho_p, R r
     return f_sqrt(q2);
 }
 
+// State of one CTA's sweep over one unit.  iter<STEADY>(k) runs both phases
+// of iteration k.  The general form (STEADY = false) checks every row range
+// and boundary rule; the steady form is used for iterations whose stages are
+// all active on interior rows, so it carries no row conditions and no
+// boundary branches and each phase compiles to one block of independent
+// work (the stages only touch different rows and ring slots).
 template <int PREC, int NT>
-__device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
-                                             const Phys<typename Types<PREC>::R>& P,
-                                             StepSmem<typename Types<PREC>::R, NT>& S) {
+struct Sweep {
     typedef typename Types<PREC>::R R;
     typedef typename Types<PREC>::TF TF;
     typedef typename Types<PREC>::TG TG;
     typedef typename Vec2<R>::T R2;
     typedef typename Vec4<R>::T R4;
 
-    const int t = threadIdx.x;
-    const int nx = I.nx, ny = I.ny, pitch = I.pitch;
-    const bool perx = I.flow[EW] == PERIODIC;
-    const bool pery = I.flow[ES] == PERIODIC;
-    const long long step = __ldcg(&I.ctl->step);
-    const int par = (int)(step & 1);
-    const bool first = step == 0;
-    // plane stride in elements; lbm_create keeps 9 planes within 2^31 elements
-    const unsigned plane = (unsigned)ny * (unsigned)pitch;
-    const TF* __restrict__ fsrc = (const TF*)I.f[par];
-    const TG* __restrict__ gsrc = (const TG*)I.g[par];
-    const R* __restrict__ Psrc = (const R*)I.P[par];
-    TF* __restrict__ fdst = (TF*)I.f[par ^ 1];
-    TG* __restrict__ gdst = (TG*)I.g[par ^ 1];
-    R* __restrict__ Pdst = (R*)I.P[par ^ 1];
-    const R rho_ref = (R)I.rho_ref;
-    const R T_ref = (R)I.T_ref;
-    const bool use_mass = P.gravity != R(0);
-    const R rho_ave = use_mass ? (R)(__ldcg(&I.ctl->mass[(step + 2) % 3]) * I.inv_n) : R(0);
-    const R cot = (R)I.cot_theta;
-    const int y0 = U.y0, y1 = U.y1, x0 = U.x0, x1 = U.x1;
-    const bool wallS = I.flow[ES] == WALL, wallN = I.flow[EN] == WALL;
+    const Inst& I;
+    const Phys<R>& P;
+    StepSmem<R, NT>& S;
+    int t, nx, ny, pitch, y0, y1;
+    bool perx, pery, first, use_mass, wallS, wallN;
+    unsigned plane;
+    const TF* __restrict__ fsrc;
+    const TG* __restrict__ gsrc;
+    const R* __restrict__ Psrc;
+    TF* __restrict__ fdst;
+    TG* __restrict__ gdst;
+    R* __restrict__ Pdst;
+    R rho_ref, T_ref, rho_ave, cot;
+    // columns
+    bool colvalid, inB, inC, inD, left_edge, right_edge;
+    bool dirW, dirE, dirS, dirN;
+    int gx, gxl, xl1, xr1, cLL, cRR, cLR, cRL;
+    R twW2, twE2, twS2, twN2, TgS_l, TgS_c, TgS_r, TgN;
+    // carried from A(k-1) to B(k-1), and the next row's loads
+    R fp[9], rhop, rhodp, jxp, jyp, psip, irp;
+    R fa[9], ga[5], pa;
+    R mass_acc;
+    int errbits;
+    int a0, a1, a2, b0, kw;
 
-    // ---- column bookkeeping (fixed for the unit)
-    const int X = x0 - 4 + t;
-    const bool colvalid = perx || (X >= 0 && X < nx);
-    const int gx = perx ? wrapi(X, nx) : X;
-    // window index of a column one or two away, clamped at open x edges
-    const int xm1 = perx ? X - 1 : min(max(X - 1, 0), nx - 1);
-    const int xp1 = perx ? X + 1 : min(max(X + 1, 0), nx - 1);
-    const int xl1 = xm1 - x0 + 4, xr1 = xp1 - x0 + 4;
-    const int cLL = (perx ? xm1 - 1 : min(max(xm1 - 1, 0), nx - 1)) - x0 + 4;
-    const int cRR = (perx ? xp1 + 1 : min(max(xp1 + 1, 0), nx - 1)) - x0 + 4;
-    const int cLR = (perx ? xm1 + 1 : min(max(xm1 + 1, 0), nx - 1)) - x0 + 4;
-    const int cRL = (perx ? xp1 - 1 : min(max(xp1 - 1, 0), nx - 1)) - x0 + 4;
-    const bool inB = colvalid && X >= x0 - 2 && X < x1 + 2;
-    const bool inC = colvalid && X >= x0 - 1 && X < x1 + 1;
-    const bool inD = X >= x0 && X < x1;
-    const bool left_edge = !perx && X == 0;
-    const bool right_edge = !perx && X == nx - 1;
+    __device__ __forceinline__ Sweep(const Inst& I_, const Unit& U, const Phys<R>& P_,
+                                     StepSmem<R, NT>& S_)
+        : I(I_), P(P_), S(S_) {
+        t = threadIdx.x;
+        nx = I.nx;
+        ny = I.ny;
+        pitch = I.pitch;
+        y0 = U.y0;
+        y1 = U.y1;
+        const int x0 = U.x0, x1 = U.x1;
+        perx = I.flow[EW] == PERIODIC;
+        pery = I.flow[ES] == PERIODIC;
+        const long long step = __ldcg(&I.ctl->step);
+        const int par = (int)(step & 1);
+        first = step == 0;
+        // plane stride in elements; lbm_create keeps 9 planes within 2^31 elements
+        plane = (unsigned)ny * (unsigned)pitch;
+        fsrc = (const TF*)I.f[par];
+        gsrc = (const TG*)I.g[par];
+        Psrc = (const R*)I.P[par];
+        fdst = (TF*)I.f[par ^ 1];
+        gdst = (TG*)I.g[par ^ 1];
+        Pdst = (R*)I.P[par ^ 1];
+        rho_ref = (R)I.rho_ref;
+        T_ref = (R)I.T_ref;
+        use_mass = P.gravity != R(0);
+        rho_ave = use_mass ? (R)(__ldcg(&I.ctl->mass[(step + 2) % 3]) * I.inv_n) : R(0);
+        cot = (R)I.cot_theta;
+        wallS = I.flow[ES] == WALL;
+        wallN = I.flow[EN] == WALL;
 
-    // thermal boundary values, as deviations from T_ref (halfway
-    // anti-bounce-back A = -g*_opp + 2 w^ (T_w - T_ref) in deviation form)
-    const bool dirW = I.therm[EW] == T_DIRICHLET, dirE = I.therm[EE] == T_DIRICHLET;
-    const bool dirS = I.therm[ES] == T_DIRICHLET, dirN = I.therm[EN] == T_DIRICHLET;
-    R twW = R(0), twE = R(0), twS = R(0), twN = R(0);
-    R TgS_l = R(0), TgS_c = R(0), TgS_r = R(0), TgN = R(0);
-    if (!perx) {
-        twW = (R)(I.T_edge[EW] - I.T_ref);
-        twE = (R)(I.T_edge[EE] - I.T_ref);
+        // ---- column bookkeeping (fixed for the unit)
+        const int X = x0 - 4 + t;
+        colvalid = perx || (X >= 0 && X < nx);
+        gx = perx ? wrapi(X, nx) : X;
+        gxl = perx ? gx : min(max(X, 0), nx - 1);   // always a valid column to load
+        // window index of a column one or two away, clamped at open x edges
+        // and to the window (threads at the window ends compute unused values)
+        const int xm1 = perx ? X - 1 : min(max(X - 1, 0), nx - 1);
+        const int xp1 = perx ? X + 1 : min(max(X + 1, 0), nx - 1);
+        auto win = [&](int c) { return min(max(c - x0 + 4, 0), NT - 1); };
+        xl1 = win(xm1);
+        xr1 = win(xp1);
+        cLL = win(perx ? xm1 - 1 : min(max(xm1 - 1, 0), nx - 1));
+        cRR = win(perx ? xp1 + 1 : min(max(xp1 + 1, 0), nx - 1));
+        cLR = win(perx ? xm1 + 1 : min(max(xm1 + 1, 0), nx - 1));
+        cRL = win(perx ? xp1 - 1 : min(max(xp1 - 1, 0), nx - 1));
+        inB = colvalid && X >= x0 - 2 && X < x1 + 2;
+        inC = colvalid && X >= x0 - 1 && X < x1 + 1;
+        inD = X >= x0 && X < x1;
+        left_edge = !perx && X == 0;
+        right_edge = !perx && X == nx - 1;
+
+        // thermal boundary values, as deviations from T_ref (halfway
+        // anti-bounce-back A = -g*_opp + 2 w^ (T_w - T_ref) in deviation form)
+        dirW = I.therm[EW] == T_DIRICHLET;
+        dirE = I.therm[EE] == T_DIRICHLET;
+        dirS = I.therm[ES] == T_DIRICHLET;
+        dirN = I.therm[EN] == T_DIRICHLET;
+        R twW = R(0), twE = R(0), twS = R(0), twN = R(0);
+        TgS_l = TgS_c = TgS_r = TgN = R(0);
+        if (!perx) {
+            twW = (R)(I.T_edge[EW] - I.T_ref);
+            twE = (R)(I.T_edge[EE] - I.T_ref);
+        }
+        if (!pery && inD) {
+            twS = (R)(wall_T(I, ES, gx) - I.T_ref);
+            twN = (R)(I.T_edge[EN] - I.T_ref);
+        }
+        if (wallS || wallN) {
+            // global columns of the window indices xl1, t, xr1
+            const int gl = perx ? wrapi(X - 1, nx) : xm1;
+            const int gr = perx ? wrapi(X + 1, nx) : xp1;
+            TgS_l = (R)wall_T(I, ES, gl);
+            TgS_c = (R)wall_T(I, ES, gx);
+            TgS_r = (R)wall_T(I, ES, gr);
+            TgN = (R)I.T_edge[EN];
+        }
+        twS2 = R(2) * P.w5_1 * twS;
+        twN2 = R(2) * P.w5_1 * twN;
+        twW2 = R(2) * P.w5_1 * twW;
+        twE2 = R(2) * P.w5_1 * twE;
+
+#pragma unroll
+        for (int q = 0; q < 9; ++q) fp[q] = R(0);
+        rhop = R(1);
+        rhodp = jxp = jyp = psip = R(0);
+        irp = R(1);
+        mass_acc = R(0);
+        errbits = 0;
+        // rotating ring slots: a0 = slot of row k, a1 = row k-1, a2 = row k-2
+        // (ring of 3, so row k-3 is a0 again); b0 = slot of row k in the ring of 5
+        a0 = 0;
+        a1 = 2;
+        a2 = 1;
+        b0 = 0;
+        // wrapped row of k for loads
+        kw = pery ? wrapi(y0 - 3, ny) : y0 - 3;
+        // the populations of the first row A works on
+        load_row(y0 - 3, kw);
     }
-    if (!pery && inD) {
-        twS = (R)(wall_T(I, ES, gx) - I.T_ref);
-        twN = (R)(I.T_edge[EN] - I.T_ref);
-    }
-    if (wallS || wallN) {
-        // global columns of the window indices xl1, t, xr1
-        const int gl = perx ? wrapi(X - 1, nx) : xm1;
-        const int gr = perx ? wrapi(X + 1, nx) : xp1;
-        TgS_l = (R)wall_T(I, ES, gl);
-        TgS_c = (R)wall_T(I, ES, gx);
-        TgS_r = (R)wall_T(I, ES, gr);
-        TgN = (R)I.T_edge[EN];
-    }
-    const R twS2 = R(2) * P.w5_1 * twS, twN2 = R(2) * P.w5_1 * twN;
-    const R twW2 = R(2) * P.w5_1 * twW, twE2 = R(2) * P.w5_1 * twE;
 
-    // registers carried from A(k-1) to B(k-1)
-    R fp[9], rhop = R(1), rhodp = R(0), jxp = R(0), jyp = R(0), psip = R(0), irp = R(1);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) fp[q] = R(0);
-    R mass_acc = R(0);   // this thread's output densities (summed in double per unit)
-    int errbits = 0;
+    __device__ __forceinline__ bool rowvalid(int r) const { return pery || (r >= 0 && r < ny); }
 
-    // rotating ring slots: a0 = slot of row k, a1 = row k-1, a2 = row k-2
-    // (ring of 3, so row k-3 is a0 again); b0 = slot of row k in the ring of 5
-    int a0 = 0, a1 = 2, a2 = 1, b0 = 0;
-    // wrapped row of k for loads
-    int kw = pery ? wrapi(y0 - 3, ny) : y0 - 3;
-
-    // populations of the row A works on, loaded one phase ahead (the loads
-    // of row k are issued before B(k-1) so their latency overlaps it)
-    R fa[9], ga[5], pa = R(0);
+    // loads of row k (wrapped row kwr) into fa, ga, pa; rows outside a
+    // non-periodic domain give zeros (A does not use them)
+    __device__ __forceinline__ void load_row(int k, int kwr) {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) fa[q] = R(0);
+        for (int q = 0; q < 9; ++q) fa[q] = R(0);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) ga[q] = R(0);
-    if (colvalid && (pery || (kw >= 0 && kw < ny))) {
-        const size_t off = (size_t)kw * pitch + gx;
-        const TF* fr = fsrc + off;
-        const TG* gr = gsrc + off;
+        for (int q = 0; q < 5; ++q) ga[q] = R(0);
+        pa = R(0);
+        if (k < y1 + 3 && rowvalid(k)) {
+            const size_t off = (size_t)kwr * pitch + gxl;
+            const TF* fr = fsrc + off;
+            const TG* gr = gsrc + off;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) fa[q] = (R)ld_st(fr + q * plane);
+            for (int q = 0; q < 9; ++q) fa[q] = (R)ld_st(fr + q * plane);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) ga[q] = (R)ld_st(gr + q * plane);
-        pa = ld_st(Psrc + off);
+            for (int q = 0; q < 5; ++q) ga[q] = (R)ld_st(gr + q * plane);
+            pa = ld_st(Psrc + off);
+        }
     }
 
-    for (int k = y0 - 3; k <= y1 + 3; ++k) {
+    template <bool STEADY>
+    __device__ __forceinline__ void iter(int k) {
         const int bC = b0 >= 3 ? b0 - 3 : b0 + 2;   // slot5(k - 3)
         const int bD = b0 >= 4 ? b0 - 4 : b0 + 1;   // slot5(k - 4)
         // ================= phase alpha =================
-        const bool doA = k < y1 + 3 && (pery || (k >= 0 && k < ny));
+        const bool doA = STEADY || (k < y1 + 3 && rowvalid(k));
 
         // ---- C(k-3): div u, grad T, Q, S and the D2Q5 MRT collision (Eq. 39)
         {
             const int r = k - 3;
-            if (r >= y0 - 1 && r < y1 + 1 && (pery || (r >= 0 && r < ny)) && inC) {
+            if (STEADY || (r >= y0 - 1 && r < y1 + 1 && rowvalid(r) && inC)) {
                 const R4 o0 = S.own[bC][0][t];
                 const R4 o1 = S.own[bC][1][t];
                 const R g0 = o0.x, g1 = o0.y, g2 = o0.z, g3 = o0.w, g4 = o1.x;
@@ -204,7 +260,7 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
                 const R dTx = -P.vs1_cs2h * m1;
                 const R dTy = -P.vs1_cs2h * m2;
                 // neighbour rows: solid -> u = 0, open -> the boundary row
-                const bool vd = pery || r - 1 >= 0, vu = pery || r + 1 < ny;
+                const bool vd = STEADY || pery || r - 1 >= 0, vu = STEADY || pery || r + 1 < ny;
                 const R2 uc = S.u[a0][t];
                 const R2 uW = S.u[a0][xl1], uE = S.u[a0][xr1];
                 R2 uS0, uS1, uS2, uN0, uN1, uN2;
@@ -242,15 +298,15 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
                 S.gs[a0][2][t] = b + h2;
                 S.gs[a0][3][t] = a - h1;
                 S.gs[a0][4][t] = b - h2;
-                if (inD && r >= y0 && r < y1) Pdst[(size_t)r * pitch + gx] = Pn;
+                if (inD && (STEADY || (r >= y0 && r < y1))) Pdst[(size_t)r * pitch + gx] = Pn;
             }
         }
 
         // ---- D9(k-3): pull streaming of f* (Eq. 6) with wall / open rules
         {
             const int r = k - 3;
-            if (r >= y0 && r < y1 && inD) {
-                const bool vd = pery || r - 1 >= 0, vu = pery || r + 1 < ny;
+            if (STEADY || (r >= y0 && r < y1 && inD)) {
+                const bool vd = STEADY || pery || r - 1 >= 0, vu = STEADY || pery || r + 1 < ny;
                 const int rowS = vd ? a1 : a0;   // source row for c_y = +1 (open: own row)
                 const int rowN = vu ? a2 : a0;   // source row for c_y = -1
                 const bool bS = !vd && wallS, bN = !vu && wallN;
@@ -269,15 +325,17 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
                     fo[7] = bN ? S.fs[a0][5][t] : S.fs[rowN][7][xr1];
                     fo[8] = bN ? S.fs[a0][6][t] : S.fs[rowN][8][xl1];
                 }
-                TF* fw = fdst + (size_t)r * pitch + gx;
+                if (inD) {
+                    TF* fw = fdst + (size_t)r * pitch + gx;
 #pragma unroll
-                for (int q = 0; q < 9; ++q) st_st(fw + q * plane, (TF)fo[q]);
+                    for (int q = 0; q < 9; ++q) st_st(fw + q * plane, (TF)fo[q]);
+                }
             }
         }
 
         // ---- A(k): moments, EOS, psi
         R rho_a = R(1), rhod_a = R(0), jx_a = R(0), jy_a = R(0), psi_a = R(0), ir_a = R(1);
-        if (doA && colvalid) {
+        if (doA && (STEADY || colvalid)) {
             rhod_a = ((fa[0] + fa[1]) + (fa[2] + fa[3])) + ((fa[4] + fa[5]) + (fa[6] + fa[7])) + fa[8];
             rho_a = rhod_a + rho_ref;
             ir_a = f_rcp(rho_a);
@@ -287,7 +345,7 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
             jy_a = (fa[2] - fa[4]) + (fa[5] + fa[6]) - (fa[7] + fa[8]);
             R q2, TdpdT;
             eos_node(P, rho_a, T_a, &q2, &TdpdT);
-            if (!(q2 >= R(0))) errbits |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
+            if (colvalid && !(q2 >= R(0))) errbits |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
             psi_a = f_sqrt(q2);
             S.psi[a0][t] = psi_a;
             S.rho[a0][t] = rho_a;
@@ -297,6 +355,8 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
             o1.x = ga[4]; o1.y = rho_a; o1.z = pa; o1.w = TdpdT;
             S.own[b0][0][t] = o0;
             S.own[b0][1][t] = o1;
+            // this unit's output rows only (steady iterations also load the
+            // three rows above the segment)
             mass_acc += (inD && k >= y0 && k < y1) ? rho_a : R(0);
         }
         __syncthreads();
@@ -306,25 +366,14 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
         R fpn[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) fpn[q] = fa[q];
-        {
-            const int kn = k + 1;
-            const int kwn = (pery && kw == ny - 1) ? 0 : kw + 1;
-            if (kn < y1 + 3 && (pery || (kn >= 0 && kn < ny)) && colvalid) {
-                const size_t off = (size_t)kwn * pitch + gx;
-                const TF* fr = fsrc + off;
-                const TG* gr = gsrc + off;
-#pragma unroll
-                for (int q = 0; q < 9; ++q) fa[q] = (R)ld_st(fr + q * plane);
-#pragma unroll
-                for (int q = 0; q < 5; ++q) ga[q] = (R)ld_st(gr + q * plane);
-                pa = ld_st(Psrc + off);
-            }
-        }
+        const int kwn = (pery && kw == ny - 1) ? 0 : kw + 1;
+        load_row(k + 1, kwn);
+
         // ---- B(k-1): interaction force, velocity, D2Q9 MRT collision
         {
             const int r = k - 1;
-            if (r >= y0 - 2 && r < y1 + 2 && (pery || (r >= 0 && r < ny)) && inB) {
-                const bool vd = pery || r - 1 >= 0, vu = pery || r + 1 < ny;
+            if (STEADY || (r >= y0 - 2 && r < y1 + 2 && rowvalid(r) && inB)) {
+                const bool vd = STEADY || pery || r - 1 >= 0, vu = STEADY || pery || r + 1 < ny;
                 R pSW, pS, pSE, pNW, pN, pNE;
                 const R pW = S.psi[a1][xl1], pE = S.psi[a1][xr1];
                 if (vd || !wallS) {
@@ -369,7 +418,7 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
                 uv.x = ux;
                 uv.y = uy;
                 S.u[a1][t] = uv;
-                if (r >= y0 - 1 && r < y1 + 1 && inC) {
+                if (STEADY || (r >= y0 - 1 && r < y1 + 1 && inC)) {
                     R* fsw = &S.fs[a1][0][t];
                     if (P.frozen_flow) {
 #pragma unroll
@@ -430,22 +479,22 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
         // ---- D5(k-4): rho c_v-weighted streaming of g* (Eq. 39)
         {
             const int r = k - 4;
-            if (r >= y0 && r < y1 && inD) {
+            if (STEADY || (r >= y0 && r < y1 && inD)) {
                 const R4 o0 = S.own[bD][0][t];
                 const R4 o1 = S.own[bD][1][t];
                 R go[5];
                 if (P.frozen_thermal) {
                     go[0] = o0.x; go[1] = o0.y; go[2] = o0.z; go[3] = o0.w; go[4] = o1.x;
                 } else {
-                    const bool vd = pery || r - 1 >= 0, vu = pery || r + 1 < ny;
+                    const bool vd = STEADY || pery || r - 1 >= 0, vu = STEADY || pery || r + 1 < ny;
                     const R* gsc = &S.gs[a1][0][t];
                     // thermal walls: halfway anti-bounce-back (Dirichlet) or
                     // bounce-back (adiabatic) supplies the incoming g*
-                    R A1, A2, A3, A4;
-                    if (left_edge) A1 = dirW ? twW2 - gsc[3 * NT] : gsc[3 * NT];
-                    else A1 = S.gs[a1][1][xl1];
-                    if (right_edge) A3 = dirE ? twE2 - gsc[1 * NT] : gsc[1 * NT];
-                    else A3 = S.gs[a1][3][xr1];
+                    const R bW = dirW ? twW2 - gsc[3 * NT] : gsc[3 * NT];
+                    const R bE = dirE ? twE2 - gsc[1 * NT] : gsc[1 * NT];
+                    const R A1 = left_edge ? bW : S.gs[a1][1][xl1];
+                    const R A3 = right_edge ? bE : S.gs[a1][3][xr1];
+                    R A2, A4;
                     if (vd) A2 = S.gs[a2][2][t];
                     else A2 = dirS ? twS2 - gsc[4 * NT] : gsc[4 * NT];
                     if (vu) A4 = S.gs[a0][4][t];
@@ -458,9 +507,11 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
                     go[3] = o0.w + (A3 - o0.w) * iC;
                     go[4] = o1.x + (A4 - o1.x) * iC;
                 }
-                TG* gw = gdst + (size_t)r * pitch + gx;
+                if (inD) {
+                    TG* gw = gdst + (size_t)r * pitch + gx;
 #pragma unroll
-                for (int q = 0; q < 5; ++q) st_st(gw + q * plane, go[q]);
+                    for (int q = 0; q < 5; ++q) st_st(gw + q * plane, go[q]);
+                }
             }
         }
         __syncthreads();
@@ -479,20 +530,40 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
         a1 = a0;
         a0 = tmp;
         b0 = b0 == 4 ? 0 : b0 + 1;
-        kw = (pery && kw == ny - 1) ? 0 : kw + 1;
+        kw = kwn;
     }
+};
 
-    if (errbits) atomicOr(&I.ctl->err, errbits);
-    if (use_mass) {
+template <int PREC, int NT>
+__device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
+                                             const Phys<typename Types<PREC>::R>& P,
+                                             StepSmem<typename Types<PREC>::R, NT>& S) {
+    Sweep<PREC, NT> w(I, U, P, S);
+    const int y0 = U.y0, y1 = U.y1;
+    // iterations whose five stages are all active on rows with interior
+    // neighbours take the steady form
+    int klo = y0 + 4, khi = y1 + 2;
+    if (!w.pery) {
+        klo = max(klo, 5);
+        khi = min(khi, I.ny - 2);
+    }
+    int k = y0 - 3;
+    for (; k < klo && k <= y1 + 3; ++k) w.template iter<false>(k);
+    for (; k <= khi; ++k) w.template iter<true>(k);
+    for (; k <= y1 + 3; ++k) w.template iter<false>(k);
+
+    if (w.errbits) atomicOr(&I.ctl->err, w.errbits);
+    if (w.use_mass) {
         // block sum of this unit's output densities -> ring slot step % 3
-        double macc = (double)mass_acc;
+        double macc = (double)w.mass_acc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) macc += __shfl_down_sync(0xffffffffu, macc, o);
-        if ((t & 31) == 0) S.red[t >> 5] = macc;
+        if ((w.t & 31) == 0) S.red[w.t >> 5] = macc;
         __syncthreads();
-        if (t == 0) {
+        if (w.t == 0) {
             double s = 0.0;
-            for (int w = 0; w < NT / 32; ++w) s += S.red[w];
+            for (int q = 0; q < NT / 32; ++q) s += S.red[q];
+            const long long step = __ldcg(&I.ctl->step);
             atomicAdd(&I.ctl->mass[step % 3], s);
         }
         __syncthreads();
