@@ -79,7 +79,7 @@ __device__ __forceinline__ R ghost_psi(const Phys<R>& P, R rho_far, R rho_p, R r
 // all active on interior rows, so it carries no row conditions and no
 // boundary branches and each phase compiles to one block of independent
 // work (the stages only touch different rows and ring slots).
-template <int PREC, int NT>
+template <int PREC, int NT, bool UNIT>
 struct Sweep {
     typedef typename Types<PREC>::R R;
     typedef typename Types<PREC>::TF TF;
@@ -288,16 +288,27 @@ struct Sweep {
                 const R Pn = Q * f_rcp(rho) * P.inv_cv;
                 const R Qs = first ? Q : Q + R(0.5) * (Q - C * Pp);
                 // moment-space collision (Eqs. 39, 40, 47), deviation form
-                const R m0s = Td + Qs;
-                const R m3s = m3d - P.vs3 * (m3d - P.w_dot * Td) + P.w_dot * Qs;
-                const R m4s = P.one_m_vs4 * m4;
                 const R h1 = R(0.5) * P.one_m_vs1 * m1, h2 = R(0.5) * P.one_m_vs1 * m2;
-                const R a = R(0.25) * (m3s + m4s), b = R(0.25) * (m3s - m4s);
-                S.gs[a0][0][t] = m0s - m3s;
-                S.gs[a0][1][t] = a + h1;
-                S.gs[a0][2][t] = b + h2;
-                S.gs[a0][3][t] = a - h1;
-                S.gs[a0][4][t] = b - h2;
+                if (UNIT) {
+                    // varsigma_3 = varsigma_4 = 1: m3* = w_dot (T + Qs), m4* = 0
+                    const R TQ = Td + Qs;
+                    const R a = R(0.25) * P.w_dot * TQ;
+                    S.gs[a0][0][t] = P.w5_0 * TQ;
+                    S.gs[a0][1][t] = a + h1;
+                    S.gs[a0][2][t] = a + h2;
+                    S.gs[a0][3][t] = a - h1;
+                    S.gs[a0][4][t] = a - h2;
+                } else {
+                    const R m0s = Td + Qs;
+                    const R m3s = m3d - P.vs3 * (m3d - P.w_dot * Td) + P.w_dot * Qs;
+                    const R m4s = P.one_m_vs4 * m4;
+                    const R a = R(0.25) * (m3s + m4s), b = R(0.25) * (m3s - m4s);
+                    S.gs[a0][0][t] = m0s - m3s;
+                    S.gs[a0][1][t] = a + h1;
+                    S.gs[a0][2][t] = b + h2;
+                    S.gs[a0][3][t] = a - h1;
+                    S.gs[a0][4][t] = b - h2;
+                }
                 if (inD && (STEADY || (r >= y0 && r < y1))) Pdst[(size_t)r * pitch + gx] = Pn;
             }
         }
@@ -423,6 +434,44 @@ struct Sweep {
                     if (P.frozen_flow) {
 #pragma unroll
                         for (int q = 0; q < 9; ++q) fsw[q * NT] = fp[q];
+                    } else if (UNIT) {
+                        // s_e = s_eps = s_q = 1: those moments leave the
+                        // collision at m^eq + F/2, so f* = M^{-1} m* needs of f
+                        // only rho, j and the stresses m_7, m_8 (Eqs. 5, 7, 8)
+                        const R* f = fp;
+                        const R rr = rhop;
+                        const R rux = rr * ux, ruy = rr * uy;
+                        const R ruu = rux * ux + ruy * uy;
+                        const R uF = ux * Fx + uy * Fy;
+                        const R Fm2 = P.negG * P.negG * (sx * sx + sy * sy);
+                        const R m7 = (f[1] + f[3]) - (f[2] + f[4]);
+                        const R m8 = (f[5] + f[7]) - (f[6] + f[8]);
+                        const R F7 = R(2) * (ux * Fx - uy * Fy);
+                        const R F8 = ux * Fy + uy * Fx;
+                        // deviation-form m*_e, m*_eps (storage shifts them by
+                        // -2 rho_ref and rho_ref)
+                        const R m1s = R(-2) * rhodp + R(3) * (ruu + uF) + R(0.5) * P.sig_e * Fm2;
+                        const R m2s = rhodp - R(3) * (ruu + uF) - R(0.5) * P.sig_eps * Fm2;
+                        const R b0 = rhodp * R(1.0 / 9.0);
+                        const R b1 = m1s * R(1.0 / 36.0), b2 = m2s * R(1.0 / 36.0);
+                        const R b7 = ((f[1] + f[3]) - (f[2] + f[4]) -
+                                      P.s_p * (m7 - (rux * ux - ruy * uy)) + P.hs_p * F7) * R(0.25);
+                        const R b8 = (m8 - P.s_p * (m8 - rux * uy) + P.hs_p * F8) * R(0.25);
+                        // j* = j + F; q* = -(j + F) / 1 -> combined axis / diagonal terms
+                        const R jxs = jxp + Fx, jys = jyp + Fy;
+                        const R X3 = jxs * R(1.0 / 3.0), Y3 = jys * R(1.0 / 3.0);
+                        const R X12 = jxs * R(1.0 / 12.0), Y12 = jys * R(1.0 / 12.0);
+                        const R cax = b0 - b1 - R(2) * b2;
+                        const R cdg = b0 + R(2) * b1 + b2;
+                        fsw[0 * NT] = b0 + R(4) * (b2 - b1);
+                        fsw[1 * NT] = cax + X3 + b7;
+                        fsw[2 * NT] = cax + Y3 - b7;
+                        fsw[3 * NT] = cax - X3 + b7;
+                        fsw[4 * NT] = cax - Y3 - b7;
+                        fsw[5 * NT] = cdg + X12 + Y12 + b8;
+                        fsw[6 * NT] = cdg - X12 + Y12 - b8;
+                        fsw[7 * NT] = cdg - X12 - Y12 + b8;
+                        fsw[8 * NT] = cdg + X12 - Y12 - b8;
                     } else {
                         const R* f = fp;
                         const R rr = rhop;
@@ -534,11 +583,11 @@ struct Sweep {
     }
 };
 
-template <int PREC, int NT>
+template <int PREC, int NT, bool UNIT>
 __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
                                              const Phys<typename Types<PREC>::R>& P,
                                              StepSmem<typename Types<PREC>::R, NT>& S) {
-    Sweep<PREC, NT> w(I, U, P, S);
+    Sweep<PREC, NT, UNIT> w(I, U, P, S);
     const int y0 = U.y0, y1 = U.y1;
     // iterations whose five stages are all active on rows with interior
     // neighbours take the steady form
@@ -570,7 +619,7 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
     }
 }
 
-template <int PREC, int NT>
+template <int PREC, int NT, bool UNIT>
 __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
     k_step(StepLaunch L, Phys<typename Types<PREC>::R> P) {
     typedef typename Types<PREC>::R R;
@@ -583,7 +632,7 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
         __syncthreads();
         if (u >= L.n_units) break;
         const Unit U = L.units[u];
-        process_unit<PREC, NT>(L.insts[U.inst], U, P, S);
+        process_unit<PREC, NT, UNIT>(L.insts[U.inst], U, P, S);
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -606,19 +655,37 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
     }
 }
 
+// The unit-rate form applies when every non-hydrodynamic rate is exactly 1
+// (s_e = s_eps = s_q = 1 and varsigma_3 = varsigma_4 = 1, the paper's choice).
+static bool unit_rates(const PhysD& d) {
+    return d.s_e == 1.0 && d.s_eps == 1.0 && d.s_q == 1.0 && d.vs3 == 1.0 && d.vs4 == 1.0;
+}
+
+template <int PREC, int NT, bool UNIT>
+static int set_smem_attr() {
+    typedef typename Types<PREC>::R R;
+    static bool done = false;
+    if (!done) {
+        if (cudaFuncSetAttribute(k_step<PREC, NT, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(StepSmem<R, NT>)) != cudaSuccess)
+            return -1;
+        done = true;
+    }
+    return 0;
+}
+
 template <int PREC, int NT>
 static int launch_one(const StepLaunch& L, cudaStream_t st) {
     typedef typename Types<PREC>::R R;
     const size_t smem = sizeof(StepSmem<R, NT>);
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(k_step<PREC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
-            return -1;
-        attr_set = true;
-    }
     Phys<R> P = make_phys<R>(L.phys);
-    k_step<PREC, NT><<<L.grid, NT, smem, st>>>(L, P);
+    if (unit_rates(L.phys)) {
+        if (set_smem_attr<PREC, NT, true>()) return -1;
+        k_step<PREC, NT, true><<<L.grid, NT, smem, st>>>(L, P);
+    } else {
+        if (set_smem_attr<PREC, NT, false>()) return -1;
+        k_step<PREC, NT, false><<<L.grid, NT, smem, st>>>(L, P);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -626,12 +693,14 @@ template <int PREC, int NT>
 static int occ_one(int* ctas, size_t* smem_bytes) {
     typedef typename Types<PREC>::R R;
     const size_t smem = sizeof(StepSmem<R, NT>);
-    if (cudaFuncSetAttribute(k_step<PREC, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (set_smem_attr<PREC, NT, true>() || set_smem_attr<PREC, NT, false>()) return -1;
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<PREC, NT, true>, NT, smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<PREC, NT, false>, NT, smem) !=
+            cudaSuccess)
         return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_step<PREC, NT>, NT, smem) !=
-        cudaSuccess)
-        return -1;
+    *ctas = a < b ? a : b;
     *smem_bytes = smem;
     return 0;
 }
