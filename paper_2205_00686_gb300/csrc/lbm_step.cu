@@ -110,7 +110,7 @@ struct Sweep {
     R fa[9], ga[5], pa;
     R mass_acc;
     int errbits;
-    int a0, a1, a2, b0, kw;
+    int ra0, ra1, ra2, b0, kw;
 
     __device__ __forceinline__ Sweep(const Inst& I_, const Unit& U, const Phys<R>& P_,
                                      StepSmem<R, NT>& S_)
@@ -204,9 +204,9 @@ struct Sweep {
         errbits = 0;
         // rotating ring slots: a0 = slot of row k, a1 = row k-1, a2 = row k-2
         // (ring of 3, so row k-3 is a0 again); b0 = slot of row k in the ring of 5
-        a0 = 0;
-        a1 = 2;
-        a2 = 1;
+        ra0 = 0;
+        ra1 = 2;
+        ra2 = 1;
         b0 = 0;
         // wrapped row of k for loads
         kw = pery ? wrapi(y0 - 3, ny) : y0 - 3;
@@ -236,8 +236,11 @@ struct Sweep {
         }
     }
 
+    // one iteration with the ring slots of rows k (a0), k - 1 (a1), k - 2 (a2);
+    // the steady loop passes them as literals, so every shared-memory ring
+    // address is a constant offset
     template <bool STEADY>
-    __device__ __forceinline__ void iter(int k) {
+    __device__ __forceinline__ void iter(int k, const int a0, const int a1, const int a2) {
         const int bC = b0 >= 3 ? b0 - 3 : b0 + 2;   // slot5(k - 3)
         const int bD = b0 >= 4 ? b0 - 4 : b0 + 1;   // slot5(k - 4)
         // ================= phase alpha =================
@@ -573,13 +576,20 @@ struct Sweep {
         jyp = jy_a;
         psip = psi_a;
         irp = ir_a;
-        // rotate the ring slots and the wrapped load row
-        const int tmp = a2;
-        a2 = a1;
-        a1 = a0;
-        a0 = tmp;
         b0 = b0 == 4 ? 0 : b0 + 1;
         kw = kwn;
+    }
+
+    // general iteration with the rotating slots
+    __device__ __forceinline__ void iter_general(int k) {
+        iter<false>(k, ra0, ra1, ra2);
+        rotate();
+    }
+    __device__ __forceinline__ void rotate() {
+        const int tmp = ra2;
+        ra2 = ra1;
+        ra1 = ra0;
+        ra0 = tmp;
     }
 };
 
@@ -596,10 +606,17 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
         klo = max(klo, 5);
         khi = min(khi, I.ny - 2);
     }
+    // the steady loop starts where the ring phase is back at its initial
+    // (0, 2, 1) and runs in groups of three with literal slots
+    klo += ((y0 - 3) - klo) % 3 + (((y0 - 3) - klo) % 3 < 0 ? 3 : 0);
     int k = y0 - 3;
-    for (; k < klo && k <= y1 + 3; ++k) w.template iter<false>(k);
-    for (; k <= khi; ++k) w.template iter<true>(k);
-    for (; k <= y1 + 3; ++k) w.template iter<false>(k);
+    for (; k < klo && k <= y1 + 3; ++k) w.iter_general(k);
+    for (; k + 2 <= khi; k += 3) {
+        w.template iter<true>(k, 0, 2, 1);
+        w.template iter<true>(k + 1, 1, 0, 2);
+        w.template iter<true>(k + 2, 2, 1, 0);
+    }
+    for (; k <= y1 + 3; ++k) w.iter_general(k);
 
     if (w.errbits) atomicOr(&I.ctl->err, w.errbits);
     if (w.use_mass) {
