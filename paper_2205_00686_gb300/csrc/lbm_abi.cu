@@ -172,7 +172,7 @@ struct lbm_ctx {
     bool initialized = false;
     int sticky = LBM_OK;
     std::string err;
-    double* fields = nullptr;  // 4 N doubles, lazily allocated
+    double* fields = nullptr;  // 5 N doubles (rho, ux, uy, T, psi scratch), lazily allocated
     void* diag_scratch = nullptr;
     double* diag_out = nullptr;
     lbm_batch* batch = nullptr;
@@ -297,7 +297,7 @@ static int ctx_check(lbm_ctx* c) {
 static int ensure_fields(lbm_ctx* c) {
     if (c->fields) return LBM_OK;
     const size_t N = (size_t)c->nx * c->ny;
-    cudaError_t e = cudaMalloc(&c->fields, 4 * N * sizeof(double));
+    cudaError_t e = cudaMalloc(&c->fields, 5 * N * sizeof(double));
     if (e != cudaSuccess) {
         c->fields = nullptr;
         return cuda_err(c, e, "cudaMalloc(fields)");
@@ -498,7 +498,7 @@ int lbm_get_rho_u_T(lbm_ctx* c, double* rho, double* ux, double* uy, double* T) 
     if (rc) return rc;
     const size_t N = (size_t)c->nx * c->ny;
     if (fields_launch(c->prec, c->inst_dev, c->inst, c->phys, c->fields, c->fields + N,
-                      c->fields + 2 * N, c->fields + 3 * N, c->stream))
+                      c->fields + 2 * N, c->fields + 3 * N, c->fields + 4 * N, c->stream))
         return cuda_err(c, cudaGetLastError(), "fields kernel");
     double* dst[4] = {rho, ux, uy, T};
     cudaError_t e = cudaSuccess;
@@ -516,7 +516,7 @@ int lbm_diagnostics(lbm_ctx* c, double rho_l, double rho_g, int sessile, lbm_dia
     if (rc) return rc;
     const size_t N = (size_t)c->nx * c->ny;
     if (fields_launch(c->prec, c->inst_dev, c->inst, c->phys, c->fields, c->fields + N,
-                      c->fields + 2 * N, c->fields + 3 * N, c->stream))
+                      c->fields + 2 * N, c->fields + 3 * N, c->fields + 4 * N, c->stream))
         return cuda_err(c, cudaGetLastError(), "fields kernel");
     if (diag_launch(c->fields, c->fields + N, c->fields + 2 * N, c->fields + 3 * N, (long long)N,
                     c->params.cv, rho_l, rho_g, c->diag_out, c->diag_scratch, c->stream))

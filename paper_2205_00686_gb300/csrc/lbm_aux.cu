@@ -53,25 +53,6 @@ int init_launch(int prec, const Inst* I_dev, const Inst& I, const double* rho, c
 
 // ---------------------------------------------------------------------------
 // fields of the current state, computed in double from the stored values
-template <int PREC>
-struct NodeReader {
-    typedef typename Types<PREC>::TF TF;
-    typedef typename Types<PREC>::TG TG;
-    const TF* f;
-    const TG* g;
-    size_t plane;
-    int pitch;
-    double rho_ref, T_ref, w_dot;
-    __device__ void rho_T(int x, int y, double* rho, double* T) const {
-        const size_t off = (size_t)y * pitch + x;
-        double r = 0.0, t = 0.0;
-        for (int i = 0; i < 9; ++i) r += (double)ld_st(f + i * plane + off) + dW9[i] * rho_ref;
-        for (int i = 0; i < 5; ++i) t += (double)ld_st(g + i * plane + off) + w5(i, w_dot) * T_ref;
-        *rho = r;
-        *T = t;
-    }
-};
-
 __device__ double psi_of(const PhysD& p, double rho, double T) {
     const double k = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
     const double Tc = 0.0778 * p.a / (0.45724 * p.b * p.Rg);
@@ -81,63 +62,60 @@ __device__ double psi_of(const PhysD& p, double rho, double T) {
     return sqrt(2.0 * (pe - rho / 3.0) / p.G);
 }
 
+// pass 1: per node rho, T, j and psi of the current state (in double)
 template <int PREC>
-__global__ void k_fields(Inst I, PhysD p, const Ctl* ctl, double* orho, double* oux,
-                         double* ouy, double* oT) {
+__global__ void k_fields_node(Inst I, PhysD p, const Ctl* ctl, double* orho, double* ojx,
+                              double* ojy, double* oT, double* opsi) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= I.nx) return;
     const long long step = __ldcg(&ctl->step);
     const int par = (int)(step & 1);
-    NodeReader<PREC> rd;
-    rd.f = (const typename Types<PREC>::TF*)I.f[par];
-    rd.g = (const typename Types<PREC>::TG*)I.g[par];
-    rd.plane = (size_t)I.ny * I.pitch;
-    rd.pitch = I.pitch;
-    rd.rho_ref = I.rho_ref;
-    rd.T_ref = I.T_ref;
-    rd.w_dot = p.w_dot;
-    const int nx = I.nx, ny = I.ny;
-    const bool perx = I.flow[EW] == PERIODIC;
-    auto extx = [&](int xx) { return perx ? wrapi(xx, nx) : min(max(xx, 0), nx - 1); };
-    const double cot = I.cot_theta;
-    // psi one layer around the domain (Section 3.3 ghost layer at walls)
-    auto psi_ext = [&](int xx, int yy) -> double {
-        const int xe = extx(xx);
-        double r, t;
-        if (yy >= 0 && yy < ny) {
-            rd.rho_T(xe, yy, &r, &t);
-            return psi_of(p, r, t);
-        }
-        const int edge = yy < 0 ? ES : EN;
-        const int kind = I.flow[edge];
-        if (kind == PERIODIC) {
-            rd.rho_T(xe, wrapi(yy, ny), &r, &t);
-            return psi_of(p, r, t);
-        }
-        if (kind == OPEN) {
-            rd.rho_T(xe, yy < 0 ? 0 : ny - 1, &r, &t);
-            return psi_of(p, r, t);
-        }
-        const int y1 = edge == ES ? 0 : ny - 1, y2 = edge == ES ? 1 : ny - 2;
-        double r2, t2, rp, tp, rm, tm, r1, t1;
-        rd.rho_T(xe, y2, &r2, &t2);
-        rd.rho_T(extx(xe + 1), y1, &rp, &tp);
-        rd.rho_T(extx(xe - 1), y1, &rm, &tm);
-        rd.rho_T(xe, y1, &r1, &t1);
-        const double rg = r2 + cot * fabs(rp - rm);
-        const double tg = I.therm[edge] == T_DIRICHLET ? wall_T(I, edge, xe) : t1;
-        return psi_of(p, rg, tg);
-    };
-    double r, t;
-    rd.rho_T(x, y, &r, &t);
-    const size_t off = (size_t)y * I.pitch + x;
-    double jx = 0.0, jy = 0.0;
+    typedef typename Types<PREC>::TF TF;
+    typedef typename Types<PREC>::TG TG;
+    const TF* f = (const TF*)I.f[par];
+    const TG* g = (const TG*)I.g[par];
+    const size_t plane = (size_t)I.ny * I.pitch, off = (size_t)y * I.pitch + x;
+    double r = 0.0, t = 0.0, jx = 0.0, jy = 0.0;
     for (int i = 0; i < 9; ++i) {
-        const double fi = (double)ld_st(rd.f + i * rd.plane + off) + dW9[i] * I.rho_ref;
+        const double fi = (double)ld_st(f + i * plane + off) + dW9[i] * I.rho_ref;
+        r += fi;
         jx += dCX9[i] * fi;
         jy += dCY9[i] * fi;
     }
+    for (int i = 0; i < 5; ++i) t += (double)ld_st(g + i * plane + off) + w5(i, p.w_dot) * I.T_ref;
+    const size_t n = (size_t)y * I.nx + x;
+    orho[n] = r;
+    oT[n] = t;
+    ojx[n] = jx;
+    ojy[n] = jy;
+    opsi[n] = psi_of(p, r, t);
+}
+
+// pass 2: F_m from the psi field (Eq. 9, wetting ghost layer of Section 3.3),
+// buoyancy, and u = (j + F/2) / rho (Eq. 11), in place over j
+__global__ void k_fields_force(Inst I, PhysD p, const Ctl* ctl, const double* rho,
+                               double* ux, double* uy, const double* T, const double* psi) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= I.nx) return;
+    const int nx = I.nx, ny = I.ny;
+    const bool perx = I.flow[EW] == PERIODIC;
+    auto extx = [&](int xx) { return perx ? wrapi(xx, nx) : min(max(xx, 0), nx - 1); };
+    auto at = [&](const double* a, int xx, int yy) { return a[(size_t)yy * nx + xx]; };
+    const double cot = I.cot_theta;
+    auto psi_ext = [&](int xx, int yy) -> double {
+        const int xe = extx(xx);
+        if (yy >= 0 && yy < ny) return at(psi, xe, yy);
+        const int edge = yy < 0 ? ES : EN;
+        const int kind = I.flow[edge];
+        if (kind == PERIODIC) return at(psi, xe, wrapi(yy, ny));
+        if (kind == OPEN) return at(psi, xe, yy < 0 ? 0 : ny - 1);
+        const int y1 = edge == ES ? 0 : ny - 1, y2 = edge == ES ? 1 : ny - 2;
+        const double rg = at(rho, xe, y2) + cot * fabs(at(rho, extx(xe + 1), y1) - at(rho, extx(xe - 1), y1));
+        const double tg = I.therm[edge] == T_DIRICHLET ? wall_T(I, edge, xe) : at(T, xe, y1);
+        return psi_of(p, rg, tg);
+    };
     double sx = 0.0, sy = 0.0;
     for (int i = 1; i < 9; ++i) {
         const double wv = i < 5 ? 1.0 / 3.0 : 1.0 / 12.0;
@@ -145,24 +123,24 @@ __global__ void k_fields(Inst I, PhysD p, const Ctl* ctl, double* orho, double* 
         sx += wv * pn * dCX9[i];
         sy += wv * pn * dCY9[i];
     }
-    const double pc = psi_of(p, r, t);
+    const size_t n = (size_t)y * nx + x;
+    const double r = rho[n], pc = psi[n];
     const double Fx = -p.G * pc * sx;
+    const long long step = __ldcg(&ctl->step);
     const double rho_ave = __ldcg(&ctl->mass[(step + 2) % 3]) * I.inv_n;
     const double Fy = -p.G * pc * sy - (r - rho_ave) * p.gravity;
-    const size_t n = (size_t)y * nx + x;
-    if (orho) orho[n] = r;
-    if (oT) oT[n] = t;
-    if (oux) oux[n] = p.frozen_flow ? 0.0 : (jx + 0.5 * Fx) / r;
-    if (ouy) ouy[n] = p.frozen_flow ? 0.0 : (jy + 0.5 * Fy) / r;
+    ux[n] = p.frozen_flow ? 0.0 : (ux[n] + 0.5 * Fx) / r;
+    uy[n] = p.frozen_flow ? 0.0 : (uy[n] + 0.5 * Fy) / r;
 }
 
 int fields_launch(int prec, const Inst* I_dev, const Inst& I, const PhysD& phys, double* rho,
-                  double* ux, double* uy, double* T, cudaStream_t st) {
+                  double* ux, double* uy, double* T, double* psi, cudaStream_t st) {
     (void)I_dev;
     dim3 blk(128), grd((I.nx + 127) / 128, I.ny);
-    if (prec == 0) k_fields<0><<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T);
-    else if (prec == 1) k_fields<1><<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T);
-    else k_fields<2><<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T);
+    if (prec == 0) k_fields_node<0><<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T, psi);
+    else if (prec == 1) k_fields_node<1><<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T, psi);
+    else k_fields_node<2><<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T, psi);
+    k_fields_force<<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T, psi);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -220,8 +220,9 @@ int step_occupancy(int prec, int threads, int* ctas_per_sm, size_t* smem_bytes);
 
 int init_launch(int prec, const Inst* I_dev, const Inst& I, const double* rho, const double* ux,
                 const double* uy, const double* T, double w_dot, cudaStream_t st);
+// rho, u (half-force velocity), T of the current state; psi is scratch of n doubles
 int fields_launch(int prec, const Inst* I_dev, const Inst& I, const PhysD& phys, double* rho,
-                  double* ux, double* uy, double* T, cudaStream_t st);
+                  double* ux, double* uy, double* T, double* psi, cudaStream_t st);
 int pop_get_launch(int prec, const Inst& I, int parity, double w_dot, double* f, double* g,
                    double* P, cudaStream_t st);
 int pop_set_launch(int prec, const Inst& I, int parity, double w_dot, const double* f,

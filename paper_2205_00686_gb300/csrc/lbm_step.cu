@@ -362,8 +362,11 @@ struct Sweep {
             if (colvalid && !(q2 >= R(0))) errbits |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
             psi_a = f_sqrt(q2);
             S.psi[a0][t] = psi_a;
-            S.rho[a0][t] = rho_a;
-            S.T[a0][t] = T_a;
+            if (wallS || wallN) {
+                // only the wetting ghost layer reads rho and T of neighbours
+                S.rho[a0][t] = rho_a;
+                S.T[a0][t] = T_a;
+            }
             R4 o0, o1;
             o0.x = ga[0]; o0.y = ga[1]; o0.z = ga[2]; o0.w = ga[3];
             o1.x = ga[4]; o1.y = rho_a; o1.z = pa; o1.w = TdpdT;
@@ -542,10 +545,11 @@ struct Sweep {
                     const R* gsc = &S.gs[a1][0][t];
                     // thermal walls: halfway anti-bounce-back (Dirichlet) or
                     // bounce-back (adiabatic) supplies the incoming g*
-                    const R bW = dirW ? twW2 - gsc[3 * NT] : gsc[3 * NT];
-                    const R bE = dirE ? twE2 - gsc[1 * NT] : gsc[1 * NT];
-                    const R A1 = left_edge ? bW : S.gs[a1][1][xl1];
-                    const R A3 = right_edge ? bE : S.gs[a1][3][xr1];
+                    R A1, A3;
+                    if (left_edge) A1 = dirW ? twW2 - gsc[3 * NT] : gsc[3 * NT];
+                    else A1 = S.gs[a1][1][xl1];
+                    if (right_edge) A3 = dirE ? twE2 - gsc[1 * NT] : gsc[1 * NT];
+                    else A3 = S.gs[a1][3][xr1];
                     R A2, A4;
                     if (vd) A2 = S.gs[a2][2][t];
                     else A2 = dirS ? twS2 - gsc[4 * NT] : gsc[4 * NT];
