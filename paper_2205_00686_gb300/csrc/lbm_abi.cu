@@ -133,13 +133,17 @@ void build_units(const Inst& I, int inst_index, int threads, int rows, std::vect
         }
 }
 
+bool has_walls(const Inst& I) {
+    return I.flow[2] == LBM_WALL || I.flow[3] == LBM_WALL;
+}
+
 // default segment height: 64 rows (7 pipeline-fill rows per segment stay
 // ~10% of the sweep) unless that leaves the persistent grid without at least
 // one unit per resident CTA; never below 8
-int default_rows(int prec, int threads, int nx, int ny) {
+int default_rows(int prec, int threads, int walls, int nx, int ny) {
     int ctas = 1;
     size_t smem = 0;
-    step_occupancy(prec, threads, &ctas, &smem);
+    step_occupancy(prec, threads, walls, &ctas, &smem);
     const long long slots = (long long)std::max(ctas, 1) * num_sms();
     const int strips = (nx + threads - 9) / (threads - 8);
     int rows = 64;
@@ -185,7 +189,7 @@ struct lbm_batch {
     Inst* insts = nullptr;
     Unit* units = nullptr;
     unsigned* sched = nullptr;
-    int n_units = 0, grid = 1, threads = 128, rows = 64, prec = -1;
+    int n_units = 0, grid = 1, threads = 128, rows = 64, prec = -1, walls = 0;
     PhysD phys;
     lbm_params params;
     cudaGraphExec_t graph = nullptr;
@@ -219,7 +223,8 @@ static int ctx_apply_tile(lbm_ctx* c, int threads, int rows) {
     build_units(c->inst, 0, threads, rows, us);
     int ctas = 1;
     size_t smem = 0;
-    if (step_occupancy(c->prec, threads, &ctas, &smem)) return set_err(c, LBM_ECUDA, "occupancy query failed");
+    if (step_occupancy(c->prec, threads, has_walls(c->inst), &ctas, &smem))
+        return set_err(c, LBM_ECUDA, "occupancy query failed");
     if (ctas < 1) return set_err(c, LBM_EINVAL, "tile does not fit on an SM");
     cudaStreamSynchronize(c->stream);
     if (c->units) cudaFree(c->units);
@@ -244,6 +249,7 @@ static StepLaunch ctx_launch(const lbm_ctx* c) {
     L.n_inst = 1;
     L.sched = c->sched;
     L.grid = c->grid;
+    L.walls = has_walls(c->inst) ? 1 : 0;
     L.phys = c->phys;
     return L;
 }
@@ -421,7 +427,8 @@ int lbm_create(int nx, int ny, const lbm_params* params, const lbm_bc* bc, int p
         threads = it->second.first;
         rows = it->second.second;
     } else {
-        rows = default_rows(prec, threads, nx, ny);
+        rows = default_rows(prec, threads, (bc->flow[2] == LBM_WALL || bc->flow[3] == LBM_WALL) ? 1 : 0,
+                            nx, ny);
     }
     int rc = ctx_apply_tile(c, threads, rows);
     if (rc) {
@@ -801,8 +808,10 @@ static int batch_rebuild(lbm_batch* b) {
     if (b->members.empty()) return LBM_OK;
     std::vector<Inst> hi;
     std::vector<Unit> us;
+    b->walls = 0;
     for (size_t i = 0; i < b->members.size(); ++i) {
         hi.push_back(b->members[i]->inst);
+        if (has_walls(b->members[i]->inst)) b->walls = 1;
         build_units(b->members[i]->inst, (int)i, b->threads, std::min(b->rows, b->members[i]->ny), us);
     }
     // longest-first is not needed: units of one batch are near-equal in size;
@@ -815,7 +824,7 @@ static int batch_rebuild(lbm_batch* b) {
     b->n_units = (int)us.size();
     int ctas = 1;
     size_t smem = 0;
-    step_occupancy(b->prec, b->threads, &ctas, &smem);
+    step_occupancy(b->prec, b->threads, b->walls, &ctas, &smem);
     b->grid = (int)std::min<long long>((long long)b->n_units, (long long)std::max(ctas, 1) * num_sms());
     return LBM_OK;
 }
@@ -890,6 +899,7 @@ int lbm_batch_step(lbm_batch* b, int n) {
     L.n_inst = (int)b->members.size();
     L.sched = b->sched;
     L.grid = b->grid;
+    L.walls = b->walls;
     L.phys = b->phys;
     int rc = enqueue_steps(b->stream, &b->graph, L, b->prec, b->threads, n, b->members[0]);
     if (rc == LBM_OK)

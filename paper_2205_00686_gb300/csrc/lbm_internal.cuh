@@ -212,11 +212,12 @@ struct StepLaunch {
     int n_inst;
     unsigned* sched;   // [0] next unit, [1] finished CTAs
     int grid;
+    int walls;         // some domain has a wall: the launch carries the wall rings
     PhysD phys;
 };
 
 int step_launch(int prec, int threads, const StepLaunch& L, cudaStream_t st);
-int step_occupancy(int prec, int threads, int* ctas_per_sm, size_t* smem_bytes);
+int step_occupancy(int prec, int threads, int walls, int* ctas_per_sm, size_t* smem_bytes);
 
 int init_launch(int prec, const Inst* I_dev, const Inst& I, const double* rho, const double* ux,
                 const double* uy, const double* T, double w_dot, cudaStream_t st);

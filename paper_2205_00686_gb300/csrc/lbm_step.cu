@@ -51,15 +51,22 @@ struct Vec4<double> { typedef double4_32a T; };
 template <class R, int NT>
 struct StepSmem {
     R psi[3][NT];
-    R rho[3][NT];
-    R T[3][NT];
     typename Vec2<R>::T u[3][NT];
     R fs[3][9][NT];     // post-collision f (deviation form)
-    R gs[3][5][NT];     // post-collision g (deviation form)
-    // per column and row: g_dev[0..4], rho, P^{n-1}, T (dp/dT)_rho
+    R gs[3][3][NT];     // post-collision g_1, g_2, g_3 (deviation form)
+    // per column and row: g_dev[0..4], rho, then P^{n-1} and T (dp/dT)_rho,
+    // which stage C replaces by the row's post-collision g*_0 and g*_4
     typename Vec4<R>::T own[5][2][NT];
     double red[NT / 32];
     int unit;
+};
+
+// rho and T rings, read only by the wetting ghost layer of walls; they follow
+// StepSmem in dynamic shared memory when a launch has a wall domain
+template <class R, int NT>
+struct WallRings {
+    R rho[3][NT];
+    R T[3][NT];
 };
 
 // ghost-layer psi of a wall (Section 3.3): rho_ghost = rho(layer 2) +
@@ -90,6 +97,7 @@ struct Sweep {
     const Inst& I;
     const Phys<R>& P;
     StepSmem<R, NT>& S;
+    WallRings<R, NT>& WR;   // valid only for domains with walls
     int t, nx, ny, pitch, y0, y1;
     bool perx, pery, first, use_mass, wallS, wallN;
     unsigned plane;
@@ -113,8 +121,8 @@ struct Sweep {
     int ra0, ra1, ra2, b0, kw;
 
     __device__ __forceinline__ Sweep(const Inst& I_, const Unit& U, const Phys<R>& P_,
-                                     StepSmem<R, NT>& S_)
-        : I(I_), P(P_), S(S_) {
+                                     StepSmem<R, NT>& S_, WallRings<R, NT>& WR_)
+        : I(I_), P(P_), S(S_), WR(WR_) {
         t = threadIdx.x;
         nx = I.nx;
         ny = I.ny;
@@ -292,26 +300,39 @@ struct Sweep {
                 const R Qs = first ? Q : Q + R(0.5) * (Q - C * Pp);
                 // moment-space collision (Eqs. 39, 40, 47), deviation form
                 const R h1 = R(0.5) * P.one_m_vs1 * m1, h2 = R(0.5) * P.one_m_vs1 * m2;
+                R gs0, gs1, gs2, gs3, gs4;
                 if (UNIT) {
                     // varsigma_3 = varsigma_4 = 1: m3* = w_dot (T + Qs), m4* = 0
                     const R TQ = Td + Qs;
                     const R a = R(0.25) * P.w_dot * TQ;
-                    S.gs[a0][0][t] = P.w5_0 * TQ;
-                    S.gs[a0][1][t] = a + h1;
-                    S.gs[a0][2][t] = a + h2;
-                    S.gs[a0][3][t] = a - h1;
-                    S.gs[a0][4][t] = a - h2;
+                    gs0 = P.w5_0 * TQ;
+                    gs1 = a + h1;
+                    gs2 = a + h2;
+                    gs3 = a - h1;
+                    gs4 = a - h2;
                 } else {
                     const R m0s = Td + Qs;
                     const R m3s = m3d - P.vs3 * (m3d - P.w_dot * Td) + P.w_dot * Qs;
                     const R m4s = P.one_m_vs4 * m4;
                     const R a = R(0.25) * (m3s + m4s), b = R(0.25) * (m3s - m4s);
-                    S.gs[a0][0][t] = m0s - m3s;
-                    S.gs[a0][1][t] = a + h1;
-                    S.gs[a0][2][t] = b + h2;
-                    S.gs[a0][3][t] = a - h1;
-                    S.gs[a0][4][t] = b - h2;
+                    gs0 = m0s - m3s;
+                    gs1 = a + h1;
+                    gs2 = b + h2;
+                    gs3 = a - h1;
+                    gs4 = b - h2;
                 }
+                // g*_1..3 are read by neighbours; g*_0 and g*_4 only by this
+                // column (rows r and r - 1 of stage D), so they go to the row's
+                // own slot in place of P^{n-1} and T (dp/dT)_rho
+                S.gs[a0][0][t] = gs1;
+                S.gs[a0][1][t] = gs2;
+                S.gs[a0][2][t] = gs3;
+                R4 oo;
+                oo.x = g4;
+                oo.y = rho;
+                oo.z = gs0;
+                oo.w = gs4;
+                S.own[bC][1][t] = oo;
                 if (inD && (STEADY || (r >= y0 && r < y1))) Pdst[(size_t)r * pitch + gx] = Pn;
             }
         }
@@ -364,8 +385,8 @@ struct Sweep {
             S.psi[a0][t] = psi_a;
             if (wallS || wallN) {
                 // only the wetting ghost layer reads rho and T of neighbours
-                S.rho[a0][t] = rho_a;
-                S.T[a0][t] = T_a;
+                WR.rho[a0][t] = rho_a;
+                WR.T[a0][t] = T_a;
             }
             R4 o0, o1;
             o0.x = ga[0]; o0.y = ga[1]; o0.z = ga[2]; o0.w = ga[3];
@@ -399,12 +420,12 @@ struct Sweep {
                 } else {
                     // south wall: layer 1 = row r (a1), layer 2 = row r + 1 (a0)
                     const bool dr = I.therm[ES] == T_DIRICHLET;
-                    pSW = ghost_psi(P, S.rho[a0][xl1], S.rho[a1][cLR], S.rho[a1][cLL], cot,
-                                    dr ? TgS_l : S.T[a1][xl1], &errbits);
-                    pS = ghost_psi(P, S.rho[a0][t], S.rho[a1][xr1], S.rho[a1][xl1], cot,
-                                   dr ? TgS_c : S.T[a1][t], &errbits);
-                    pSE = ghost_psi(P, S.rho[a0][xr1], S.rho[a1][cRR], S.rho[a1][cRL], cot,
-                                    dr ? TgS_r : S.T[a1][xr1], &errbits);
+                    pSW = ghost_psi(P, WR.rho[a0][xl1], WR.rho[a1][cLR], WR.rho[a1][cLL], cot,
+                                    dr ? TgS_l : WR.T[a1][xl1], &errbits);
+                    pS = ghost_psi(P, WR.rho[a0][t], WR.rho[a1][xr1], WR.rho[a1][xl1], cot,
+                                   dr ? TgS_c : WR.T[a1][t], &errbits);
+                    pSE = ghost_psi(P, WR.rho[a0][xr1], WR.rho[a1][cRR], WR.rho[a1][cRL], cot,
+                                    dr ? TgS_r : WR.T[a1][xr1], &errbits);
                 }
                 if (vu || !wallN) {
                     const int s = vu ? a0 : a1;
@@ -412,12 +433,12 @@ struct Sweep {
                 } else {
                     // north wall: layer 1 = row r (a1), layer 2 = row r - 1 (a2)
                     const bool dr = I.therm[EN] == T_DIRICHLET;
-                    pNW = ghost_psi(P, S.rho[a2][xl1], S.rho[a1][cLR], S.rho[a1][cLL], cot,
-                                    dr ? TgN : S.T[a1][xl1], &errbits);
-                    pN = ghost_psi(P, S.rho[a2][t], S.rho[a1][xr1], S.rho[a1][xl1], cot,
-                                   dr ? TgN : S.T[a1][t], &errbits);
-                    pNE = ghost_psi(P, S.rho[a2][xr1], S.rho[a1][cRR], S.rho[a1][cRL], cot,
-                                    dr ? TgN : S.T[a1][xr1], &errbits);
+                    pNW = ghost_psi(P, WR.rho[a2][xl1], WR.rho[a1][cLR], WR.rho[a1][cLL], cot,
+                                    dr ? TgN : WR.T[a1][xl1], &errbits);
+                    pN = ghost_psi(P, WR.rho[a2][t], WR.rho[a1][xr1], WR.rho[a1][xl1], cot,
+                                   dr ? TgN : WR.T[a1][t], &errbits);
+                    pNE = ghost_psi(P, WR.rho[a2][xr1], WR.rho[a1][cRR], WR.rho[a1][cRL], cot,
+                                    dr ? TgN : WR.T[a1][xr1], &errbits);
                 }
                 // Eq. 9 with varpi(1) = 1/3, varpi(2) = 1/12
                 const R sx = (pE - pW) * R(1.0 / 3.0) + ((pNE - pSW) + (pSE - pNW)) * R(1.0 / 12.0);
@@ -542,20 +563,22 @@ struct Sweep {
                     go[0] = o0.x; go[1] = o0.y; go[2] = o0.z; go[3] = o0.w; go[4] = o1.x;
                 } else {
                     const bool vd = STEADY || pery || r - 1 >= 0, vu = STEADY || pery || r + 1 < ny;
+                    // gs planes hold g*_1, g*_2, g*_3; g*_0 and g*_4 of row r sit
+                    // in the row's own slot, g*_4 of row r + 1 in that row's
                     const R* gsc = &S.gs[a1][0][t];
                     // thermal walls: halfway anti-bounce-back (Dirichlet) or
                     // bounce-back (adiabatic) supplies the incoming g*
                     R A1, A3;
-                    if (left_edge) A1 = dirW ? twW2 - gsc[3 * NT] : gsc[3 * NT];
-                    else A1 = S.gs[a1][1][xl1];
-                    if (right_edge) A3 = dirE ? twE2 - gsc[1 * NT] : gsc[1 * NT];
-                    else A3 = S.gs[a1][3][xr1];
+                    if (left_edge) A1 = dirW ? twW2 - gsc[2 * NT] : gsc[2 * NT];
+                    else A1 = S.gs[a1][0][xl1];
+                    if (right_edge) A3 = dirE ? twE2 - gsc[0] : gsc[0];
+                    else A3 = S.gs[a1][2][xr1];
                     R A2, A4;
-                    if (vd) A2 = S.gs[a2][2][t];
-                    else A2 = dirS ? twS2 - gsc[4 * NT] : gsc[4 * NT];
-                    if (vu) A4 = S.gs[a0][4][t];
-                    else A4 = dirN ? twN2 - gsc[2 * NT] : gsc[2 * NT];
-                    const R A0 = gsc[0];
+                    if (vd) A2 = S.gs[a2][1][t];
+                    else A2 = dirS ? twS2 - o1.w : o1.w;
+                    if (vu) A4 = S.own[bC][1][t].w;
+                    else A4 = dirN ? twN2 - gsc[1 * NT] : gsc[1 * NT];
+                    const R A0 = o1.z;
                     const R iC = f_rcp(o1.y * P.cv);
                     go[0] = o0.x + (A0 - o0.x) * iC;
                     go[1] = o0.y + (A1 - o0.y) * iC;
@@ -600,8 +623,9 @@ struct Sweep {
 template <int PREC, int NT, bool UNIT>
 __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
                                              const Phys<typename Types<PREC>::R>& P,
-                                             StepSmem<typename Types<PREC>::R, NT>& S) {
-    Sweep<PREC, NT, UNIT> w(I, U, P, S);
+                                             StepSmem<typename Types<PREC>::R, NT>& S,
+                                             WallRings<typename Types<PREC>::R, NT>& WR) {
+    Sweep<PREC, NT, UNIT> w(I, U, P, S, WR);
     const int y0 = U.y0, y1 = U.y1;
     // iterations whose five stages are all active on rows with interior
     // neighbours take the steady form
@@ -646,6 +670,7 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
     typedef typename Types<PREC>::R R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<R, NT>& S = *reinterpret_cast<StepSmem<R, NT>*>(smem_raw);
+    WallRings<R, NT>& WR = *reinterpret_cast<WallRings<R, NT>*>(smem_raw + sizeof(StepSmem<R, NT>));
     for (;;) {
         if (threadIdx.x == 0) S.unit = (int)atomicAdd(&L.sched[0], 1u);
         __syncthreads();
@@ -653,7 +678,7 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
         __syncthreads();
         if (u >= L.n_units) break;
         const Unit U = L.units[u];
-        process_unit<PREC, NT, UNIT>(L.insts[U.inst], U, P, S);
+        process_unit<PREC, NT, UNIT>(L.insts[U.inst], U, P, S, WR);
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -682,13 +707,18 @@ static bool unit_rates(const PhysD& d) {
     return d.s_e == 1.0 && d.s_eps == 1.0 && d.s_q == 1.0 && d.vs3 == 1.0 && d.vs4 == 1.0;
 }
 
+template <int PREC, int NT>
+static size_t smem_for(bool walls) {
+    typedef typename Types<PREC>::R R;
+    return sizeof(StepSmem<R, NT>) + (walls ? sizeof(WallRings<R, NT>) : 0);
+}
+
 template <int PREC, int NT, bool UNIT>
 static int set_smem_attr() {
-    typedef typename Types<PREC>::R R;
     static bool done = false;
     if (!done) {
         if (cudaFuncSetAttribute(k_step<PREC, NT, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(StepSmem<R, NT>)) != cudaSuccess)
+                                 (int)smem_for<PREC, NT>(true)) != cudaSuccess)
             return -1;
         done = true;
     }
@@ -698,7 +728,7 @@ static int set_smem_attr() {
 template <int PREC, int NT>
 static int launch_one(const StepLaunch& L, cudaStream_t st) {
     typedef typename Types<PREC>::R R;
-    const size_t smem = sizeof(StepSmem<R, NT>);
+    const size_t smem = smem_for<PREC, NT>(L.walls != 0);
     Phys<R> P = make_phys<R>(L.phys);
     if (unit_rates(L.phys)) {
         if (set_smem_attr<PREC, NT, true>()) return -1;
@@ -711,9 +741,8 @@ static int launch_one(const StepLaunch& L, cudaStream_t st) {
 }
 
 template <int PREC, int NT>
-static int occ_one(int* ctas, size_t* smem_bytes) {
-    typedef typename Types<PREC>::R R;
-    const size_t smem = sizeof(StepSmem<R, NT>);
+static int occ_one(int walls, int* ctas, size_t* smem_bytes) {
+    const size_t smem = smem_for<PREC, NT>(walls != 0);
     if (set_smem_attr<PREC, NT, true>() || set_smem_attr<PREC, NT, false>()) return -1;
     int a = 0, b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<PREC, NT, true>, NT, smem) !=
@@ -737,15 +766,15 @@ int step_launch(int prec, int threads, const StepLaunch& L, cudaStream_t st) {
     return launch_one<2, 256>(L, st);
 }
 
-int step_occupancy(int prec, int threads, int* ctas, size_t* smem) {
+int step_occupancy(int prec, int threads, int walls, int* ctas, size_t* smem) {
     if (threads == 128) {
-        if (prec == 0) return occ_one<0, 128>(ctas, smem);
-        if (prec == 1) return occ_one<1, 128>(ctas, smem);
-        return occ_one<2, 128>(ctas, smem);
+        if (prec == 0) return occ_one<0, 128>(walls, ctas, smem);
+        if (prec == 1) return occ_one<1, 128>(walls, ctas, smem);
+        return occ_one<2, 128>(walls, ctas, smem);
     }
-    if (prec == 0) return occ_one<0, 256>(ctas, smem);
-    if (prec == 1) return occ_one<1, 256>(ctas, smem);
-    return occ_one<2, 256>(ctas, smem);
+    if (prec == 0) return occ_one<0, 256>(walls, ctas, smem);
+    if (prec == 1) return occ_one<1, 256>(walls, ctas, smem);
+    return occ_one<2, 256>(walls, ctas, smem);
 }
 
 }  // namespace lbm

@@ -66,9 +66,10 @@ def test_ragged_multi_tile_fp64(name, tile):
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 2e-4), ("fp32_g16", 2e-3)])
 @pytest.mark.parametrize("name", ["open_dirichlet", "wall_open_heater"])
-def test_ragged_multi_tile_reduced_precision(prec, tol, name):
-    c = P.droplet_case(250, 75, P.bc_variants()[name], gravity=3e-5)
-    fe, pe, g, o = P.compare(c, 200, prec)
+@pytest.mark.parametrize("tile", [None, (256, 40)])
+def test_ragged_multi_tile_reduced_precision(prec, tol, name, tile):
+    c = P.droplet_case(600, 75, P.bc_variants()[name], gravity=3e-5)
+    fe, pe, g, o = P.compare(c, 200, prec, tile=tile)
     print(prec, name, fe)
     assert fe["rho"] <= tol and fe["T"] <= tol
 
@@ -114,8 +115,9 @@ def test_tiles_give_identical_results():
         else:
             r = ref[tile[0]]
             assert np.array_equal(r[0], f) and np.array_equal(r[1], g), tile
-    assert P.rel_err(ref[128][0], ref[256][0]) < 1e-6
-    assert P.rel_err(ref[128][1], ref[256][1]) < 1e-6
+    for th in (256,):
+        assert P.rel_err(ref[128][0], ref[th][0]) < 1e-6
+        assert P.rel_err(ref[128][1], ref[th][1]) < 1e-6
 
 
 def test_diagnostics_match_oracle():
