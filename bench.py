@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tile", default=None,
+                    help="THREADS,ROWS: fixed tile instead of the autotuner (profiler captures)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-instances", type=int, default=512)
     ap.add_argument("--serve-steps", type=int, default=500)
@@ -258,7 +260,9 @@ def run_ours(args):
 
     dom = lbm.Domain(case.nx, case.ny, case.params, case.bc, prec="fp32",
                      stream=stream.cuda_stream)
-    if not args.no_tune:
+    if args.tile:
+        dom.set_tile(*[int(v) for v in args.tile.split(",")])
+    elif not args.no_tune:
         dom.autotune(10)          # tile chosen by timed trials on a scratch domain
     dom.init_fields(*case.fields())
     with ClockSampler(local) as clk:
