@@ -16,7 +16,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_SRCS = [os.path.join(_HERE, "lbm_oracle.c"), os.path.join(_HERE, "lbm_oracle_analysis.c")]
 _HDR = os.path.join(_HERE, "lbm_oracle.h")
 LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
 
@@ -27,12 +27,12 @@ EDGE_W, EDGE_E, EDGE_S, EDGE_N = 0, 1, 2, 3
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(f) for f in _SRCS + [_HDR])
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
         return LIB_PATH
     tmp = LIB_PATH + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c99", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC",
-           "-shared", "-o", tmp, _SRC, "-lm"]
+           "-shared", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
@@ -59,8 +59,22 @@ class Diag(ctypes.Structure):
         ("step", ctypes.c_long), ("nonfinite", ctypes.c_int)]
 
 
+class Contact(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "theta_deg", "xc", "yc", "radius", "base_width", "height")] + [
+        ("n_points", ctypes.c_int)]
+
+
+class Component(ctypes.Structure):
+    _fields_ = [("label", ctypes.c_longlong), ("area", ctypes.c_longlong),
+                ("sum_y", ctypes.c_longlong), ("y_min", ctypes.c_int), ("y_max", ctypes.c_int),
+                ("touches_w", ctypes.c_int), ("touches_e", ctypes.c_int),
+                ("touches_s", ctypes.c_int), ("touches_n", ctypes.c_int)]
+
+
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
 
 
 def lib():
@@ -94,6 +108,15 @@ def lib():
         L.orc_diagnostics.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, ctypes.POINTER(Diag)]
         L.orc_last_error.argtypes = [ctypes.c_void_p]
+        L.orc_reconfigure.argtypes = [ctypes.c_void_p, P, B]
+        L.orc_interface_points.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_int, _dp, _dp, ctypes.c_int]
+        L.orc_circle_fit.argtypes = [_dp, _dp, ctypes.c_int, _dp]
+        L.orc_contact_angle.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_int, ctypes.POINTER(Contact)]
+        L.orc_components.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_int, _ip,
+                                     ctypes.POINTER(Component), ctypes.c_int, _ip]
         _lib = L
     return _lib
 
@@ -177,6 +200,57 @@ def matrices():
     return M.reshape(9, 9), Mi.reshape(9, 9), Mh.reshape(5, 5), Mhi.reshape(5, 5)
 
 
+# ---- interface analyses on a density field ------------------------------
+
+def interface_points(rho, rho_mid: float, skip_rows: int = 0):
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    ny, nx = rho.shape
+    n = lib().orc_interface_points(_ptr(rho), nx, ny, rho_mid, skip_rows, None, None, 0)
+    if n < 0:
+        raise OracleError(n)
+    px, py = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+    lib().orc_interface_points(_ptr(rho), nx, ny, rho_mid, skip_rows, _ptr(px), _ptr(py), n)
+    return px[:n], py[:n]
+
+
+def circle_fit(px, py):
+    px = np.ascontiguousarray(px, dtype=np.float64)
+    py = np.ascontiguousarray(py, dtype=np.float64)
+    out = np.zeros(3)
+    rc = lib().orc_circle_fit(_ptr(px), _ptr(py), len(px), _ptr(out))
+    if rc:
+        raise OracleError(rc)
+    return tuple(out)
+
+
+def contact_angle(rho, rho_l: float, rho_g: float, skip_rows: int = 3) -> dict:
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    ny, nx = rho.shape
+    c = Contact()
+    rc = lib().orc_contact_angle(_ptr(rho), nx, ny, rho_l, rho_g, skip_rows, ctypes.byref(c))
+    if rc:
+        raise OracleError(rc)
+    return {k: getattr(c, k) for k, _ in Contact._fields_}
+
+
+def components(rho, threshold: float, below: bool = True, periodic_x: bool = False,
+               periodic_y: bool = False):
+    """Returns (labels [ny][nx] int32, list of component dicts sorted by label)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    ny, nx = rho.shape
+    labels = np.zeros((ny, nx), dtype=np.int32)
+    n = ctypes.c_int(0)
+    cap = nx * ny
+    comps = (Component * max(cap, 1))()
+    rc = lib().orc_components(_ptr(rho), nx, ny, int(periodic_x), int(periodic_y), threshold,
+                              int(below), labels.ctypes.data_as(_ip), comps, cap,
+                              ctypes.byref(n))
+    if rc:
+        raise OracleError(rc)
+    out = [{k: getattr(comps[i], k) for k, _ in Component._fields_} for i in range(n.value)]
+    return labels, out
+
+
 # ---- simulation ----------------------------------------------------------
 
 class OracleError(RuntimeError):
@@ -251,3 +325,10 @@ class Sim:
     @property
     def last_error(self) -> int:
         return lib().orc_last_error(self._h)
+
+    def reconfigure(self, params: dict, bc: dict):
+        self._p = make_params(params)
+        self._b = make_bc(bc)
+        rc = lib().orc_reconfigure(self._h, ctypes.byref(self._p), ctypes.byref(self._b))
+        if rc:
+            raise OracleError(rc)

@@ -807,3 +807,30 @@ int orc_diagnostics(orc_sim* s, double rho_l, double rho_g, int sessile, orc_dia
     d->step = s->step;
     return ORC_OK;
 }
+
+/* ---------------------------------------------------------------------- */
+/* reconfiguration between steps (Section 4.2: the sessile droplet is first */
+/* relaxed without evaporation to its contact angle, then the wall heats)   */
+
+int orc_reconfigure(orc_sim* s, const orc_params* p, const orc_bc* bc) {
+    if (!s || !p || !bc || !valid_bc(s->nx, s->ny, bc) || p->cv <= 0 || p->nu <= 0 ||
+        p->lambda <= 0 || p->w_dot != s->p.w_dot)
+        return ORC_EINVAL;
+    /* the flow boundary kinds fix the geometry of the problem */
+    for (int e = 0; e < 4; ++e)
+        if (bc->flow[e] != s->bc.flow[e]) return ORC_EINVAL;
+    s->p = *p;
+    s->bc = *bc;
+    s->Tc = orc_Tc(p);
+    s->kpr = pr_k(p);
+    s->sp = 1.0 / (3.0 * p->nu + 0.5);
+    s->cs2h = p->w_dot / 2.0;
+    s->vs12 = 1.0 / (p->lambda / s->cs2h + 0.5);
+    s->cot_theta = tan(M_PI / 2.0 - bc->theta_deg * M_PI / 180.0);
+    d2q5_weights(p, s->w5);
+    double S[9] = {p->s0, p->s_e, p->s_eps, p->s_j, p->s_q, p->s_j, p->s_q, s->sp, s->sp};
+    memcpy(s->S, S, sizeof(S));
+    double L[5] = {p->vs0, s->vs12, s->vs12, p->vs3, p->vs4};
+    memcpy(s->Lam, L, sizeof(L));
+    return ORC_OK;
+}

@@ -10,8 +10,9 @@
  * Every field array is row-major [ny][nx] (x fastest), node (0,0) at the
  * south-west corner.  Populations are [q][ny][nx].  Everything is double.
  *
- * Parity status per function (see the header of lbm_oracle.c for the pins):
- *   all functions declared here are pinned by tests in tests/test_oracle_*.py.
+ * Parity status per function (see the headers of lbm_oracle.c and
+ * lbm_oracle_analysis.c for the pins): all functions declared here are pinned
+ * by tests in tests/test_oracle_*.py.
  */
 #ifndef LBM_ORACLE_H
 #define LBM_ORACLE_H
@@ -78,6 +79,24 @@ typedef struct {
     int nonfinite;
 } orc_diag;
 
+/* contact angle of a sessile droplet on the south wall (Section 4.2) */
+typedef struct {
+    double theta_deg;        /* angle inside the liquid */
+    double xc, yc, radius;   /* fitted circle, lattice units, node (0,0) at origin */
+    double base_width;       /* chord of the circle on the wall line y = -1/2 */
+    double height;           /* apex height above the wall line */
+    int n_points;            /* interface points in the fit */
+} orc_contact;
+
+/* one 4-connected region of the vapour (or liquid) phase */
+typedef struct {
+    long long label;         /* smallest node index y * nx + x in the region */
+    long long area;          /* nodes */
+    long long sum_y;         /* sum of the nodes' row indices */
+    int y_min, y_max;
+    int touches_w, touches_e, touches_s, touches_n;
+} orc_component;
+
 typedef struct orc_sim orc_sim;
 
 /* derived constants and closed forms ---------------------------------- */
@@ -105,6 +124,24 @@ int orc_set_populations(orc_sim* s, const double* f, const double* g, const doub
 long orc_step_count(const orc_sim* s);
 int orc_diagnostics(orc_sim* s, double rho_l, double rho_g, int sessile, orc_diag* d);
 int orc_last_error(const orc_sim* s);
+/* replaces params and boundary values between steps; the flow boundary kinds
+ * and w_dot must stay as created (ORC_EINVAL otherwise) */
+int orc_reconfigure(orc_sim* s, const orc_params* p, const orc_bc* bc);
+
+/* interface analyses on a density field [ny][nx] (lbm_oracle_analysis.c) -- */
+/* interface points rho = rho_mid on lattice links at rows >= skip_rows; writes
+ * at most max_points and returns the total count (or ORC_EINVAL) */
+int orc_interface_points(const double* rho, int nx, int ny, double rho_mid, int skip_rows,
+                         double* px, double* py, int max_points);
+/* algebraic least-squares circle through n >= 3 points: out = (xc, yc, R) */
+int orc_circle_fit(const double* px, const double* py, int n, double out[3]);
+int orc_contact_angle(const double* rho, int nx, int ny, double rho_l, double rho_g,
+                      int skip_rows, orc_contact* out);
+/* labels [ny][nx]: the component label, -1 outside the phase; comps sorted by
+ * label (at most max_comps written); *n_comps = number of components */
+int orc_components(const double* rho, int nx, int ny, int periodic_x, int periodic_y,
+                   double threshold, int below, int* labels, orc_component* comps,
+                   int max_comps, int* n_comps);
 
 #ifdef __cplusplus
 }

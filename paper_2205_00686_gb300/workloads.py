@@ -186,6 +186,51 @@ def nucleate_boiling(nx=300, ny=600, gravity=2e-5, heater_w=20, T_sat=0.86, T_h=
                 steps, rl, rg)
 
 
+def sessile_cap(nx=160, ny=80, R=30.0, theta=90.0, w=4.0, Tr=0.86, x0=None, amp=0.0,
+                seed=6, top=OPEN, steps=0, p=None) -> Case:
+    """Sessile droplet whose initial shape is a circular cap meeting the south
+    wall line y = -1/2 at the angle `theta` (inside the liquid): the circle of
+    radius R is centred at (x0, -1/2 - R cos(theta)), with the tanh profile of
+    Eq. 57 across its boundary.  Isothermal at Tr T_c; periodic in x; the wall
+    and the top are held at that temperature."""
+    rg, rl = COEXISTENCE[Tr]
+    x0 = 0.5 * (nx - 1) if x0 is None else x0
+    yc = -0.5 - R * np.cos(np.radians(theta))
+    rho = tanh_disc(nx, ny, x0, yc, R, w, rl, rg)
+    if amp:
+        rho = rho + noise(seed, (ny, nx), amp)
+    T = np.full((ny, nx), Tr * TC)
+    z = np.zeros((ny, nx))
+    bc = bc_spec([PERIODIC, PERIODIC, WALL, top],
+                 [T_PERIODIC, T_PERIODIC, T_DIRICHLET, T_DIRICHLET],
+                 T_edge=[0.0, 0.0, Tr * TC, Tr * TC], theta_deg=theta)
+    return Case("sessile_cap_%dx%d_%g" % (nx, ny, theta), nx, ny, p or params(), bc,
+                rho, z, z.copy(), T, steps, rl, rg, sessile=True)
+
+
+def bubble_field(nx, ny, bubbles, w=4.0, Tr=0.86, periodic_x=False, periodic_y=False,
+                 amp=0.0, seed=7):
+    """Liquid at rest with vapour bubbles: `bubbles` lists (x0, y0, R); each
+    bubble is a tanh disc (Eq. 57) around its centre, distances taken across
+    the seams of periodic axes.  Returns (rho, T) at Tr T_c."""
+    rg, rl = COEXISTENCE[Tr]
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    vap = np.zeros((ny, nx))
+    for (x0, y0, R) in bubbles:
+        dx = np.abs(x - x0)
+        dy = np.abs(y - y0)
+        if periodic_x:
+            dx = np.minimum(dx, nx - dx)
+        if periodic_y:
+            dy = np.minimum(dy, ny - dy)
+        d = np.sqrt(dx ** 2 + dy ** 2)
+        vap = np.maximum(vap, 0.5 - 0.5 * np.tanh((d - R) / (0.5 * w)))
+    rho = rl - (rl - rg) * vap
+    if amp:
+        rho = rho + noise(seed, (ny, nx), amp)
+    return rho, np.full((ny, nx), Tr * TC)
+
+
 def batch_instances(n=512, seed=5, side_lo=64, side_hi=512, steps=5000):
     """The batched / served population: open-space evaporating droplets with
     square sides uniform in [side_lo, side_hi], radii 0.2-0.3 of the side and
