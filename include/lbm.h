@@ -190,6 +190,69 @@ void lbm_destroy(lbm_ctx* ctx);
 /* Human-readable text of the last error seen by this context (never NULL). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 
+/* Replaces the physical parameters and the boundary values of a context
+ * between steps.  Section 4.2 relaxes a sessile droplet without evaporation
+ * until it shows the prescribed contact angle and only then heats the wall:
+ * run with frozen_thermal = 1 and the wall at the saturation temperature,
+ * then call this with frozen_thermal = 0 and the heated wall.
+ *  params: as for lbm_create; w_dot must be unchanged (the stored thermal
+ *          deviations depend on it) and rho_ref / T_ref are ignored (the
+ *          storage references set at initialisation stay).
+ *  bc:     the flow kind of every edge must be unchanged (the geometry of the
+ *          problem); thermal kinds, edge temperatures, the contact angle and
+ *          the heater may change.
+ * Takes effect for the next queued step.  LBM_EINVAL on a violated rule,
+ * LBM_ESTATE while the context is attached to a batch. */
+int lbm_reconfigure(lbm_ctx* ctx, const lbm_params* params, const lbm_bc* bc);
+
+/* Contact angle of a sessile droplet on the south wall (Section 4.2).  The
+ * interface is rho_mid = (rho_l + rho_g)/2; each horizontal or vertical
+ * lattice link whose two densities lie on opposite sides of it gives one
+ * point, linearly interpolated on the link; links touching rows below
+ * skip_rows (the wetting ghost layer distorts the first rows) are left out.
+ * A circle is fitted to the points by algebraic least squares and the angle
+ * inside the liquid is taken where it meets the wall line y = -1/2 (halfway
+ * bounce-back): cos(theta) = (-1/2 - y_c)/R.  The field must hold one droplet
+ * that does not cross a periodic seam.  Sums are accumulated in double on
+ * the device in a fixed order (the result does not vary between runs).
+ * Synchronises.  LBM_EINVAL if the south edge is not a wall, rho_l <= rho_g,
+ * skip_rows < 0 or fewer than 3 points (out->n_points is then still set). */
+typedef struct {
+    double theta_deg;        /* contact angle inside the liquid, degrees */
+    double xc, yc, radius;   /* fitted circle, lattice units, node (0,0) at origin */
+    double base_width;       /* chord of the circle on the wall line */
+    double height;           /* apex height above the wall line */
+    int n_points;            /* interface points in the fit */
+} lbm_contact;
+int lbm_contact_angle(lbm_ctx* ctx, double rho_l, double rho_g, int skip_rows, lbm_contact* out);
+
+/* 4-connected regions of one phase of the current density field: nodes with
+ * rho < threshold (below != 0, vapour) or rho > threshold (below == 0,
+ * liquid), connected across the seams of periodic axes.  Each region's label
+ * is the smallest node index y * nx + x it contains (unique, independent of
+ * the order of work on the device).  A bubble has departed from the south
+ * wall (Section 4.3) when its region no longer touches row 0; its equivalent
+ * diameter is 2 sqrt(area / pi).
+ *  labels:   host int array [ny][nx] receiving each node's label, -1 outside
+ *            the phase; may be NULL.
+ *  regions:  host array of max_regions entries, filled in increasing label
+ *            order; may be NULL when max_regions is 0.
+ *  n_regions: receives the number of regions; when it exceeds max_regions,
+ *            the max_regions regions with the smallest labels are written.
+ * Device scratch of 32 bytes per node is allocated on first use and kept
+ * with the context.  Synchronises.  LBM_EINVAL on bad arguments, LBM_ECUDA if
+ * the labelling reports that a capped loop ran out (it cannot by
+ * construction; the cap guards against a defect). */
+typedef struct {
+    long long label;         /* smallest node index in the region */
+    long long area;          /* nodes */
+    long long sum_y;         /* sum of the nodes' row indices (centroid height) */
+    int y_min, y_max;        /* row range */
+    int touches_w, touches_e, touches_s, touches_n;   /* has a node on that edge */
+} lbm_region;
+int lbm_regions(lbm_ctx* ctx, double threshold, int below, int* labels, lbm_region* regions,
+                int max_regions, int* n_regions);
+
 /* ---- batched stepping of independent domains --------------------------- *
  * A batch advances every attached context by one coupled step per launch of
  * one persistent kernel that walks a shared work list of (domain, tile)

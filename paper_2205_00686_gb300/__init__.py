@@ -37,7 +37,8 @@ ABI_FUNCTIONS = (
     "lbm_step_count", "lbm_sync", "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
     "lbm_batch_create", "lbm_batch_attach", "lbm_batch_detach", "lbm_batch_size",
     "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy", "lbm_set_tile", "lbm_get_tile",
-    "lbm_autotune", "lbm_diag_reduce_noalloc",
+    "lbm_autotune", "lbm_diag_reduce_noalloc", "lbm_reconfigure", "lbm_contact_angle",
+    "lbm_regions",
 )
 
 
@@ -66,6 +67,19 @@ class lbm_diag(ctypes.Structure):
         "mass", "energy", "liquid_mass", "liquid_area", "liquid_area_smooth",
         "diameter", "diameter_smooth", "max_u")] + [
         ("step", ctypes.c_longlong), ("nonfinite", ctypes.c_int)]
+
+
+class lbm_contact(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "theta_deg", "xc", "yc", "radius", "base_width", "height")] + [
+        ("n_points", ctypes.c_int)]
+
+
+class lbm_region(ctypes.Structure):
+    _fields_ = [("label", ctypes.c_longlong), ("area", ctypes.c_longlong),
+                ("sum_y", ctypes.c_longlong), ("y_min", ctypes.c_int), ("y_max", ctypes.c_int),
+                ("touches_w", ctypes.c_int), ("touches_e", ctypes.c_int),
+                ("touches_s", ctypes.c_int), ("touches_n", ctypes.c_int)]
 
 
 _lib = None
@@ -115,6 +129,12 @@ def lib():
             "lbm_diag_reduce_noalloc": ([_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, _vp, _vp],
                                         ctypes.c_int),
+            "lbm_reconfigure": ([_vp, P, B], ctypes.c_int),
+            "lbm_contact_angle": ([_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   ctypes.POINTER(lbm_contact)], ctypes.c_int),
+            "lbm_regions": ([_vp, ctypes.c_double, ctypes.c_int, _vp,
+                             ctypes.POINTER(lbm_region), ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -265,6 +285,40 @@ class Domain:
     @property
     def last_error(self) -> str:
         return lib().lbm_last_error(self._h).decode()
+
+    def reconfigure(self, params: dict, bc: dict):
+        """New params / boundary values for the following steps (flow boundary
+        kinds and w_dot fixed)."""
+        self._p = make_params(params)
+        self._b = make_bc(bc)
+        _check(lib().lbm_reconfigure(self._h, ctypes.byref(self._p), ctypes.byref(self._b)),
+               self._h)
+
+    def contact_angle(self, rho_l, rho_g, skip_rows: int = 3) -> dict:
+        c = lbm_contact()
+        _check(lib().lbm_contact_angle(self._h, rho_l, rho_g, int(skip_rows), ctypes.byref(c)),
+               self._h)
+        return {k: getattr(c, k) for k, _ in lbm_contact._fields_}
+
+    def regions(self, threshold: float, below: bool = True, labels: bool = False,
+                max_regions: int = 4096):
+        """Regions of the phase rho < threshold (below) or rho > threshold, as
+        a list of dicts sorted by label, plus the label field if asked."""
+        lab = np.empty((self.ny, self.nx), dtype=np.int32) if labels else None
+        n = ctypes.c_int(0)
+        buf = (lbm_region * max(int(max_regions), 1))()
+        _check(lib().lbm_regions(self._h, float(threshold), int(bool(below)),
+                                 lab.ctypes.data if lab is not None else None, buf,
+                                 int(max_regions), ctypes.byref(n)), self._h)
+        out = [{k: getattr(buf[i], k) for k, _ in lbm_region._fields_}
+               for i in range(min(n.value, int(max_regions)))]
+        return (out, lab) if labels else out
+
+    def region_count(self, threshold: float, below: bool = True) -> int:
+        n = ctypes.c_int(0)
+        _check(lib().lbm_regions(self._h, float(threshold), int(bool(below)), None, None, 0,
+                                 ctypes.byref(n)), self._h)
+        return n.value
 
 
 def lbm_diag_reduce_noalloc(rho, ux, uy, T, n, cv, rho_l, rho_g, out7, stream=None) -> int:

@@ -55,6 +55,11 @@ bool bc_valid(int nx, int ny, const lbm_bc* bc) {
     return true;
 }
 
+bool params_valid(const lbm_params* p) {
+    return p->cv > 0 && p->nu > 0 && p->lambda > 0 && p->w_dot > 0 && p->w_dot < 1 &&
+           p->G != 0.0 && p->b > 0 && p->s_e > 0 && p->s_e < 2 && p->s_eps > 0 && p->s_eps < 2;
+}
+
 PhysD phys_from(const lbm_params* p) {
     PhysD d;
     d.a = p->a;
@@ -179,6 +184,8 @@ struct lbm_ctx {
     double* fields = nullptr;  // 5 N doubles (rho, ux, uy, T, psi scratch), lazily allocated
     void* diag_scratch = nullptr;
     double* diag_out = nullptr;
+    void* iface_scratch = nullptr;   // contact-angle partial sums + 12 results
+    void* region_scratch = nullptr;  // 32 bytes per node, lazily allocated
     lbm_batch* batch = nullptr;
 };
 
@@ -194,6 +201,12 @@ struct lbm_batch {
     lbm_params params;
     cudaGraphExec_t graph = nullptr;
 };
+
+// a context attached to a batch is stepped on the batch's stream: wait for it
+// before reading the state on the context's own stream
+static void ctx_settle(lbm_ctx* c) {
+    if (c->batch) cudaStreamSynchronize(c->batch->stream);
+}
 
 static int set_err(lbm_ctx* c, int code, const char* msg) {
     if (c) c->err = msg;
@@ -347,11 +360,7 @@ int lbm_create(int nx, int ny, const lbm_params* params, const lbm_bc* bc, int p
     if (nx > (1 << 20) || ny > (1 << 20)) return LBM_EINVAL;
     // the kernels address the 9 planes of f with 32-bit element offsets
     if ((unsigned long long)layout_for(nx, ny, prec).pitch * ny * 9ull >= (1ull << 31)) return LBM_EINVAL;
-    if (!bc_valid(nx, ny, bc)) return LBM_EINVAL;
-    if (!(params->cv > 0) || !(params->nu > 0) || !(params->lambda > 0) ||
-        !(params->w_dot > 0 && params->w_dot < 1) || params->G == 0.0 || !(params->b > 0) ||
-        !(params->s_e > 0 && params->s_e < 2) || !(params->s_eps > 0 && params->s_eps < 2))
-        return LBM_EINVAL;
+    if (!bc_valid(nx, ny, bc) || !params_valid(params)) return LBM_EINVAL;
     if (device_mem && ((uintptr_t)device_mem % kAlign || device_bytes < lbm_state_bytes(nx, ny, prec)))
         return LBM_EINVAL;
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
@@ -501,6 +510,7 @@ int lbm_sync(lbm_ctx* c) {
 int lbm_get_rho_u_T(lbm_ctx* c, double* rho, double* ux, double* uy, double* T) {
     if (!c) return LBM_EINVAL;
     if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    ctx_settle(c);
     int rc = ensure_fields(c);
     if (rc) return rc;
     const size_t N = (size_t)c->nx * c->ny;
@@ -519,6 +529,7 @@ int lbm_get_rho_u_T(lbm_ctx* c, double* rho, double* ux, double* uy, double* T) 
 int lbm_diagnostics(lbm_ctx* c, double rho_l, double rho_g, int sessile, lbm_diag* out) {
     if (!c || !out || !(rho_l > rho_g)) return LBM_EINVAL;
     if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    ctx_settle(c);
     int rc = ensure_fields(c);
     if (rc) return rc;
     const size_t N = (size_t)c->nx * c->ny;
@@ -549,6 +560,7 @@ int lbm_diagnostics(lbm_ctx* c, double rho_l, double rho_g, int sessile, lbm_dia
 int lbm_get_populations(lbm_ctx* c, double* f, double* g, double* P) {
     if (!c) return LBM_EINVAL;
     if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    ctx_settle(c);
     const size_t N = (size_t)c->nx * c->ny;
     double* buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, 15 * N * sizeof(double));
@@ -634,6 +646,7 @@ static size_t ckpt_payload(const lbm_ctx* c) {
 int lbm_save(lbm_ctx* c, const char* path) {
     if (!c || !path) return LBM_EINVAL;
     if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    ctx_settle(c);
     int rc = ctx_check(c);
     if (rc) return rc;
     Ctl h;
@@ -724,6 +737,8 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->fields) cudaFree(c->fields);
     if (c->diag_scratch) cudaFree(c->diag_scratch);
     if (c->diag_out) cudaFree(c->diag_out);
+    if (c->iface_scratch) cudaFree(c->iface_scratch);
+    if (c->region_scratch) cudaFree(c->region_scratch);
     if (c->small) cudaFree(c->small);
     if (c->own_mem && c->mem) cudaFree(c->mem);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -733,6 +748,167 @@ void lbm_destroy(lbm_ctx* c) {
 const char* lbm_last_error(const lbm_ctx* c) {
     if (!c) return "null context";
     return c->err.c_str();
+}
+
+// ---- reconfiguration and interface analyses -----------------------------
+int lbm_reconfigure(lbm_ctx* c, const lbm_params* params, const lbm_bc* bc) {
+    if (!c || !params || !bc) return LBM_EINVAL;
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    if (!params_valid(params) || !bc_valid(c->nx, c->ny, bc))
+        return set_err(c, LBM_EINVAL, "invalid parameters or boundaries");
+    if (params->w_dot != c->params.w_dot) return set_err(c, LBM_EINVAL, "w_dot cannot change");
+    for (int e = 0; e < 4; ++e)
+        if (bc->flow[e] != c->bc.flow[e]) return set_err(c, LBM_EINVAL, "flow boundary kinds cannot change");
+    lbm_params np = *params;
+    np.rho_ref = c->params.rho_ref;
+    np.T_ref = c->params.T_ref;
+    c->params = np;
+    c->bc = *bc;
+    c->phys = phys_from(&np);
+    Inst& I = c->inst;
+    for (int k = 0; k < 4; ++k) {
+        I.therm[k] = bc->therm[k];
+        I.T_edge[k] = bc->T_edge[k];
+    }
+    I.heater_x0 = bc->heater_x0;
+    I.heater_x1 = bc->heater_x1;
+    I.T_heater = bc->T_heater;
+    I.cot_theta = tan(M_PI / 2.0 - bc->theta_deg * M_PI / 180.0);
+    // the captured graph holds the old constants as launch arguments
+    drop_graph(&c->graph);
+    return ctx_upload_inst(c);
+}
+
+int lbm_contact_angle(lbm_ctx* c, double rho_l, double rho_g, int skip_rows, lbm_contact* out) {
+    if (!c || !out || !(rho_l > rho_g) || skip_rows < 0) return LBM_EINVAL;
+    memset(out, 0, sizeof(*out));
+    if (c->bc.flow[LBM_EDGE_S] != LBM_WALL) return set_err(c, LBM_EINVAL, "no south wall");
+    if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    ctx_settle(c);
+    int rc = ensure_fields(c);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!c->iface_scratch) {
+        e = cudaMalloc(&c->iface_scratch, iface_scratch_bytes() + 16 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemset(c->iface_scratch, 0, iface_scratch_bytes() + 16 * sizeof(double));
+        if (e != cudaSuccess) {
+            if (c->iface_scratch) cudaFree(c->iface_scratch);
+            c->iface_scratch = nullptr;
+            return cuda_err(c, e, "cudaMalloc(contact-angle scratch)");
+        }
+    }
+    const size_t N = (size_t)c->nx * c->ny;
+    double* res = (double*)((char*)c->iface_scratch + iface_scratch_bytes());
+    if (fields_launch(c->prec, c->inst_dev, c->inst, c->phys, c->fields, c->fields + N,
+                      c->fields + 2 * N, c->fields + 3 * N, c->fields + 4 * N, c->stream) ||
+        iface_launch(c->fields, c->nx, c->ny, 0.5 * (rho_l + rho_g), skip_rows, res,
+                     c->iface_scratch, c->stream))
+        return cuda_err(c, cudaGetLastError(), "contact-angle kernels");
+    double h[12];
+    e = cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "contact angle");
+    rc = ctx_check(c);
+    if (rc) return rc;
+    const double n = h[0];
+    out->n_points = (int)n;
+    if (n < 3) return set_err(c, LBM_EINVAL, "fewer than 3 interface points");
+    // normal equations of min sum (z + D u + E v + F)^2 about the mean point,
+    // solved by Cramer's rule
+    const double Su = h[1], Sv = h[2], Suu = h[3], Svv = h[4], Suv = h[5];
+    const double Suz = h[6], Svz = h[7], Sz = h[8];
+    const double A[3][3] = {{Suu, Suv, Su}, {Suv, Svv, Sv}, {Su, Sv, n}};
+    const double b[3] = {-Suz, -Svz, -Sz};
+    auto det3 = [](const double M[3][3]) {
+        return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+               M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+               M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    };
+    const double d = det3(A);
+    if (!(fabs(d) > 0.0)) return set_err(c, LBM_EINVAL, "degenerate interface points");
+    double sol[3];
+    for (int k = 0; k < 3; ++k) {
+        double M[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 3; ++q) M[r][q] = q == k ? b[r] : A[r][q];
+        sol[k] = det3(M) / d;
+    }
+    const double uc = -0.5 * sol[0], vc = -0.5 * sol[1];
+    const double R2 = uc * uc + vc * vc - sol[2];
+    if (!(R2 > 0.0)) return set_err(c, LBM_EINVAL, "no circle through the interface points");
+    const double xm = h[10] / h[9], ym = h[11] / h[9];
+    out->xc = xm + uc;
+    out->yc = ym + vc;
+    out->radius = sqrt(R2);
+    const double yw = -0.5;   // halfway bounce-back wall line
+    double cs = (yw - out->yc) / out->radius;
+    cs = cs < -1.0 ? -1.0 : (cs > 1.0 ? 1.0 : cs);
+    out->theta_deg = acos(cs) * (180.0 / M_PI);
+    const double hh = R2 - (yw - out->yc) * (yw - out->yc);
+    out->base_width = hh > 0.0 ? 2.0 * sqrt(hh) : 0.0;
+    out->height = out->yc + out->radius - yw;
+    return LBM_OK;
+}
+
+int lbm_regions(lbm_ctx* c, double threshold, int below, int* labels, lbm_region* regions,
+                int max_regions, int* n_regions) {
+    if (!c || !n_regions || max_regions < 0 || (max_regions > 0 && !regions)) return LBM_EINVAL;
+    *n_regions = 0;
+    if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    ctx_settle(c);
+    int rc = ensure_fields(c);
+    if (rc) return rc;
+    const long long N = (long long)c->nx * c->ny;
+    cudaError_t e = cudaSuccess;
+    if (!c->region_scratch) {
+        e = cudaMalloc(&c->region_scratch, regions_scratch_bytes(N));
+        if (e != cudaSuccess) {
+            c->region_scratch = nullptr;
+            return cuda_err(c, e, "cudaMalloc(region scratch)");
+        }
+    }
+    int *parent = nullptr, *roots = nullptr, *count = nullptr;
+    if (fields_launch(c->prec, c->inst_dev, c->inst, c->phys, c->fields, c->fields + N,
+                      c->fields + 2 * N, c->fields + 3 * N, c->fields + 4 * N, c->stream) ||
+        regions_launch(c->fields, c->nx, c->ny, c->bc.flow[LBM_EDGE_W] == LBM_PERIODIC,
+                       c->bc.flow[LBM_EDGE_S] == LBM_PERIODIC, threshold, below,
+                       c->region_scratch, (int)N, &parent, &roots, &count, c->stream))
+        return cuda_err(c, cudaGetLastError(), "region kernels");
+    int hc[2];
+    e = cudaMemcpyAsync(hc, count, sizeof(hc), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && labels)
+        e = cudaMemcpyAsync(labels, parent, N * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "region labels");
+    if (hc[1]) return set_err(c, LBM_ECUDA, "region labelling did not converge");
+    const int m = hc[0];
+    *n_regions = m;
+    if (max_regions > 0 && m > 0) {
+        RegionOut* dev = nullptr;
+        e = cudaMalloc(&dev, (size_t)m * sizeof(RegionOut));
+        if (e != cudaSuccess) return cuda_err(c, e, "cudaMalloc(regions)");
+        std::vector<RegionOut> h(m);
+        if (regions_gather_launch(c->region_scratch, N, m, dev, c->stream)) e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h.data(), dev, (size_t)m * sizeof(RegionOut), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(dev);
+        if (e != cudaSuccess) return cuda_err(c, e, "region statistics");
+        std::sort(h.begin(), h.end(), [](const RegionOut& a, const RegionOut& b) { return a.label < b.label; });
+        for (int k = 0; k < m && k < max_regions; ++k) {
+            lbm_region& r = regions[k];
+            r.label = h[k].label;
+            r.area = h[k].area;
+            r.sum_y = h[k].sum_y;
+            r.y_min = h[k].y_min;
+            r.y_max = h[k].y_max;
+            r.touches_w = (h[k].flags >> 0) & 1;
+            r.touches_e = (h[k].flags >> 1) & 1;
+            r.touches_s = (h[k].flags >> 2) & 1;
+            r.touches_n = (h[k].flags >> 3) & 1;
+        }
+    }
+    return ctx_check(c);
 }
 
 // ---- tile / autotune ------------------------------------------------------

@@ -235,4 +235,24 @@ int diag_launch(const double* rho, const double* ux, const double* uy, const dou
                 long long n, double cv, double rho_l, double rho_g, double* out9,
                 void* scratch, cudaStream_t st);
 
+// interface analyses (lbm_analysis.cu)
+// contact-angle sums: out12[0..8] = n, sum u, sum v, sum uu, sum vv, sum uv,
+// sum u z, sum v z, sum z about the mean point, out12[9..11] = n, sum x, sum y
+size_t iface_scratch_bytes();
+int iface_launch(const double* rho, int nx, int ny, double rho_mid, int skip, double* out12,
+                 void* scratch, cudaStream_t st);
+// one region of the phase: label = smallest node index, flags bit 0..3 = the
+// region touches the W, E, S, N edge
+struct RegionOut {
+    long long label, area, sum_y;
+    int y_min, y_max, flags, pad;
+};
+size_t regions_scratch_bytes(long long n);
+// labels the phase; *parent_out -> n ints (root label or -1), *roots_out ->
+// the first max_roots roots in no order, *count_out -> [roots found, error]
+int regions_launch(const double* rho, int nx, int ny, int perx, int pery, double thr, int below,
+                   void* scratch, int max_roots, int** parent_out, int** roots_out,
+                   int** count_out, cudaStream_t st);
+int regions_gather_launch(void* scratch, long long n, int m, RegionOut* out, cudaStream_t st);
+
 }  // namespace lbm

@@ -214,17 +214,28 @@ def bubble_field(nx, ny, bubbles, w=4.0, Tr=0.86, periodic_x=False, periodic_y=F
     bubble is a tanh disc (Eq. 57) around its centre, distances taken across
     the seams of periodic axes.  Returns (rho, T) at Tr T_c."""
     rg, rl = COEXISTENCE[Tr]
-    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
     vap = np.zeros((ny, nx))
     for (x0, y0, R) in bubbles:
-        dx = np.abs(x - x0)
-        dy = np.abs(y - y0)
-        if periodic_x:
-            dx = np.minimum(dx, nx - dx)
-        if periodic_y:
-            dy = np.minimum(dy, ny - dy)
-        d = np.sqrt(dx ** 2 + dy ** 2)
-        vap = np.maximum(vap, 0.5 - 0.5 * np.tanh((d - R) / (0.5 * w)))
+        # the profile is evaluated within R + 10 w of the centre; beyond it
+        # the tanh tail is below 1e-17
+        h = int(np.ceil(R + 10.0 * w))
+
+        def axis(c, n, per):
+            idx = np.arange(int(np.floor(c)) - h, int(np.floor(c)) + h + 2)
+            if per:
+                dist = np.abs(idx - c)
+                idx = idx % n
+                dist = np.minimum(dist, n - dist)
+                keep = np.unique(idx, return_index=True)[1]
+                return idx[keep], dist[keep]
+            idx = idx[(idx >= 0) & (idx < n)]
+            return idx, np.abs(idx - c)
+
+        xi, dx = axis(x0, nx, periodic_x)
+        yi, dy = axis(y0, ny, periodic_y)
+        d = np.sqrt(dx[None, :] ** 2 + dy[:, None] ** 2)
+        win = np.ix_(yi, xi)
+        vap[win] = np.maximum(vap[win], 0.5 - 0.5 * np.tanh((d - R) / (0.5 * w)))
     rho = rl - (rl - rg) * vap
     if amp:
         rho = rho + noise(seed, (ny, nx), amp)
