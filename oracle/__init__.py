@@ -16,7 +16,8 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "lbm_oracle.c"), os.path.join(_HERE, "lbm_oracle_analysis.c")]
+_SRCS = [os.path.join(_HERE, "lbm_oracle.c"), os.path.join(_HERE, "lbm_oracle_analysis.c"),
+         os.path.join(_HERE, "lbm_oracle3d.c")]
 _HDR = os.path.join(_HERE, "lbm_oracle.h")
 LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
 
@@ -57,6 +58,11 @@ class Diag(ctypes.Structure):
         "mass", "energy", "liquid_mass", "liquid_area", "liquid_area_smooth",
         "diameter", "diameter_smooth", "max_u")] + [
         ("step", ctypes.c_long), ("nonfinite", ctypes.c_int)]
+
+
+class BC3(ctypes.Structure):
+    _fields_ = [("flow_z", ctypes.c_int), ("therm", ctypes.c_int * 2),
+                ("T_edge", ctypes.c_double * 2), ("theta_deg", ctypes.c_double)]
 
 
 class Contact(ctypes.Structure):
@@ -109,6 +115,26 @@ def lib():
                                       ctypes.c_int, ctypes.POINTER(Diag)]
         L.orc_last_error.argtypes = [ctypes.c_void_p]
         L.orc_reconfigure.argtypes = [ctypes.c_void_p, P, B]
+        B3 = ctypes.POINTER(BC3)
+        _i19 = ctypes.POINTER(ctypes.c_int)
+        L.orc3_velocities.argtypes = [_i19, _i19, _i19, _dp]
+        L.orc3_matrices.argtypes = [_dp, _dp, _dp, _dp]
+        L.orc3_feq.argtypes = [ctypes.c_double] * 4 + [_dp]
+        L.orc3_force_term.argtypes = [ctypes.c_double] * 6 + [_dp]
+        L.orc3_create.restype = ctypes.c_void_p
+        L.orc3_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, B3,
+                                  ctypes.POINTER(ctypes.c_int)]
+        L.orc3_destroy.argtypes = [ctypes.c_void_p]
+        L.orc3_init.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp, _dp]
+        L.orc3_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc3_fields.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp, _dp]
+        L.orc3_get_populations.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+        L.orc3_set_populations.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_long,
+                                           ctypes.c_double]
+        L.orc3_step_count.restype = ctypes.c_long
+        L.orc3_step_count.argtypes = [ctypes.c_void_p]
+        L.orc3_diagnostics.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, ctypes.POINTER(Diag)]
         L.orc_interface_points.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_int, _dp, _dp, ctypes.c_int]
         L.orc_circle_fit.argtypes = [_dp, _dp, ctypes.c_int, _dp]
@@ -240,13 +266,17 @@ def components(rho, threshold: float, below: bool = True, periodic_x: bool = Fal
     ny, nx = rho.shape
     labels = np.zeros((ny, nx), dtype=np.int32)
     n = ctypes.c_int(0)
-    cap = nx * ny
-    comps = (Component * max(cap, 1))()
-    rc = lib().orc_components(_ptr(rho), nx, ny, int(periodic_x), int(periodic_y), threshold,
-                              int(below), labels.ctypes.data_as(_ip), comps, cap,
-                              ctypes.byref(n))
-    if rc:
-        raise OracleError(rc)
+    cap = min(nx * ny, 4096)
+    while True:
+        comps = (Component * max(cap, 1))()
+        rc = lib().orc_components(_ptr(rho), nx, ny, int(periodic_x), int(periodic_y),
+                                  threshold, int(below), labels.ctypes.data_as(_ip), comps, cap,
+                                  ctypes.byref(n))
+        if rc:
+            raise OracleError(rc)
+        if n.value <= cap:
+            break
+        cap = n.value
     out = [{k: getattr(comps[i], k) for k, _ in Component._fields_} for i in range(n.value)]
     return labels, out
 
@@ -332,3 +362,105 @@ class Sim:
         rc = lib().orc_reconfigure(self._h, ctypes.byref(self._p), ctypes.byref(self._b))
         if rc:
             raise OracleError(rc)
+
+
+# ---- three-dimensional form ------------------------------------------------
+
+def make_bc3(d: dict) -> BC3:
+    b = BC3()
+    b.flow_z = int(d["flow_z"])
+    for e in range(2):
+        b.therm[e] = int(d["therm"][e])
+        b.T_edge[e] = float(d.get("T_edge", (0.0, 0.0))[e])
+    b.theta_deg = float(d.get("theta_deg", 90.0))
+    return b
+
+
+def velocities3():
+    cx, cy, cz = (ctypes.c_int * 19)(), (ctypes.c_int * 19)(), (ctypes.c_int * 19)()
+    w = np.zeros(19)
+    lib().orc3_velocities(cx, cy, cz, _ptr(w))
+    return np.array(list(cx)), np.array(list(cy)), np.array(list(cz)), w
+
+
+def matrices3():
+    M, Mi, Mh, Mhi = np.zeros(361), np.zeros(361), np.zeros(49), np.zeros(49)
+    lib().orc3_matrices(_ptr(M), _ptr(Mi), _ptr(Mh), _ptr(Mhi))
+    return M.reshape(19, 19), Mi.reshape(19, 19), Mh.reshape(7, 7), Mhi.reshape(7, 7)
+
+
+def feq3(rho, ux, uy, uz):
+    out = np.zeros(19)
+    lib().orc3_feq(rho, ux, uy, uz, _ptr(out))
+    return out
+
+
+def force_term3(ux, uy, uz, Fx, Fy, Fz):
+    out = np.zeros(19)
+    lib().orc3_force_term(ux, uy, uz, Fx, Fy, Fz, _ptr(out))
+    return out
+
+
+class Sim3:
+    """One FP64 CPU simulation of an nx x ny x nz domain (3-D form)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, params: dict, bc3: dict):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self._p = make_params(params)
+        self._b = make_bc3(bc3)
+        err = ctypes.c_int(0)
+        self._h = lib().orc3_create(nx, ny, nz, ctypes.byref(self._p), ctypes.byref(self._b),
+                                    ctypes.byref(err))
+        if not self._h:
+            raise OracleError(err.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().orc3_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def _shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def init(self, rho, ux, uy, uz, T):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self._shape())
+                for a in (rho, ux, uy, uz, T)]
+        rc = lib().orc3_init(self._h, *[_ptr(a) for a in arrs])
+        if rc:
+            raise OracleError(rc)
+
+    def step(self, n: int = 1, check: bool = True) -> int:
+        rc = lib().orc3_step(self._h, int(n))
+        if rc and check:
+            raise OracleError(rc)
+        return rc
+
+    @property
+    def step_count(self) -> int:
+        return lib().orc3_step_count(self._h)
+
+    def fields(self):
+        out = [np.zeros(self._shape()) for _ in range(5)]
+        lib().orc3_fields(self._h, *[_ptr(a) for a in out])
+        return tuple(out)
+
+    def populations(self):
+        f = np.zeros((19,) + self._shape())
+        g = np.zeros((7,) + self._shape())
+        P = np.zeros(self._shape())
+        lib().orc3_get_populations(self._h, _ptr(f), _ptr(g), _ptr(P))
+        return f, g, P
+
+    def set_populations(self, f, g, P, step: int, rho_ave_prev: float):
+        f, g, P = (np.ascontiguousarray(a, dtype=np.float64) for a in (f, g, P))
+        rc = lib().orc3_set_populations(self._h, _ptr(f), _ptr(g), _ptr(P), int(step),
+                                        float(rho_ave_prev))
+        if rc:
+            raise OracleError(rc)
+
+    def diagnostics(self, rho_l: float, rho_g: float, sessile: bool = False) -> dict:
+        d = Diag()
+        lib().orc3_diagnostics(self._h, rho_l, rho_g, int(sessile), ctypes.byref(d))
+        return {k: getattr(d, k) for k, _ in Diag._fields_}

@@ -143,6 +143,36 @@ int orc_components(const double* rho, int nx, int ny, int periodic_x, int period
                    double threshold, int below, int* labels, orc_component* comps,
                    int max_comps, int* n_comps);
 
+/* three-dimensional form (lbm_oracle3d.c): D3Q19 MRT flow lattice, D3Q7
+ * temperature lattice with the same weighted streaming.  x and y periodic;
+ * z periodic or walls at both ends.  Arrays are [nz][ny][nx] (x fastest),
+ * populations [q][nz][ny][nx]; gravity acts along -z. -------------------- */
+typedef struct {
+    int flow_z;          /* ORC_PERIODIC or ORC_WALL (bottom and top) */
+    int therm[2];        /* bottom, top: ORC_T_* (periodic iff flow_z is) */
+    double T_edge[2];    /* bottom, top wall temperatures */
+    double theta_deg;    /* contact angle of both walls */
+} orc_bc3;
+typedef struct orc3_sim orc3_sim;
+void orc3_velocities(int cx[19], int cy[19], int cz[19], double w[19]);
+void orc3_matrices(double M[361], double Minv[361], double Mh[49], double Mhinv[49]);
+void orc3_feq(double rho, double ux, double uy, double uz, double f[19]);
+void orc3_force_term(double ux, double uy, double uz, double Fx, double Fy, double Fz,
+                     double out[19]);
+orc3_sim* orc3_create(int nx, int ny, int nz, const orc_params* p, const orc_bc3* bc, int* err);
+void orc3_destroy(orc3_sim* s);
+int orc3_init(orc3_sim* s, const double* rho, const double* ux, const double* uy,
+              const double* uz, const double* T);
+int orc3_step(orc3_sim* s, int n);
+int orc3_fields(orc3_sim* s, double* rho, double* ux, double* uy, double* uz, double* T);
+int orc3_get_populations(const orc3_sim* s, double* f, double* g, double* P);
+int orc3_set_populations(orc3_sim* s, const double* f, const double* g, const double* P,
+                         long step, double rho_ave_prev);
+long orc3_step_count(const orc3_sim* s);
+/* as orc_diagnostics; liquid_area is the liquid volume and the diameters are
+ * those of the equivalent sphere (hemisphere when sessile) */
+int orc3_diagnostics(orc3_sim* s, double rho_l, double rho_g, int sessile, orc_diag* d);
+
 #ifdef __cplusplus
 }
 #endif

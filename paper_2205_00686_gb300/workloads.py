@@ -256,3 +256,81 @@ def batch_instances(n=512, seed=5, side_lo=64, side_hi=512, steps=5000):
         c.name = "batch%03d_%d" % (k, side)
         out.append(c)
     return out
+
+
+# ---- three-dimensional form ------------------------------------------------
+
+def periodic_bc3() -> dict:
+    return dict(flow_z=PERIODIC, therm=[T_PERIODIC, T_PERIODIC], T_edge=[0.0, 0.0],
+                theta_deg=90.0)
+
+
+def wall_bc3(T_bottom, T_top, theta_deg=90.0, adiabatic=(False, False)) -> dict:
+    """Walls at both z ends, Dirichlet at the given temperatures (or adiabatic)."""
+    th = [T_ADIABATIC if a else T_DIRICHLET for a in adiabatic]
+    return dict(flow_z=WALL, therm=th, T_edge=[float(T_bottom), float(T_top)],
+                theta_deg=float(theta_deg))
+
+
+class Case3:
+    """A 3-D simulation input: sizes, params, bc and fields [nz][ny][nx]."""
+
+    def __init__(self, name, nx, ny, nz, params, bc, rho, T, steps, rho_l, rho_g,
+                 sessile=False):
+        self.name, self.nx, self.ny, self.nz = name, nx, ny, nz
+        self.params, self.bc = params, bc
+        self.rho, self.T = rho, T
+        z = np.zeros_like(rho)
+        self.ux, self.uy, self.uz = z, z.copy(), z.copy()
+        self.steps, self.rho_l, self.rho_g, self.sessile = steps, rho_l, rho_g, sessile
+
+    def fields(self):
+        return self.rho, self.ux, self.uy, self.uz, self.T
+
+
+def tanh_ball(nx, ny, nz, x0, y0, z0, R, w, inside, outside):
+    """Eq. 57 around a sphere; nodes at integer coordinates."""
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(np.float64)
+    d = np.sqrt((x - x0) ** 2 + (y - y0) ** 2 + (z - z0) ** 2)
+    return 0.5 * (inside + outside) - 0.5 * (inside - outside) * np.tanh((d - R) / (0.5 * w))
+
+
+def droplet3d(nx=32, ny=32, nz=32, R=8.0, w=4.0, Tr=0.86, amp=1e-4, seed=8, steps=1000,
+              p=None) -> Case3:
+    """Static droplet in a periodic box at uniform T."""
+    rg, rl = COEXISTENCE[Tr]
+    rho = tanh_ball(nx, ny, nz, 0.5 * (nx - 1), 0.5 * (ny - 1), 0.5 * (nz - 1), R, w, rl, rg)
+    if amp:
+        rho = rho + noise(seed, rho.shape, amp)
+    T = np.full(rho.shape, Tr * TC)
+    return Case3("droplet3d_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, p or params(),
+                 periodic_bc3(), rho, T, steps, rl, rg)
+
+
+def heated_droplet3d(nx=64, ny=64, nz=64, R=16.0, w=4.0, T_sat=0.86, T_wall=0.95, amp=1e-4,
+                     seed=9, steps=1000, p=None) -> Case3:
+    """Droplet at T_sat between two walls at T_wall (z ends), periodic in x
+    and y: it evaporates as heat conducts in from the walls."""
+    rg, rl = COEXISTENCE[T_sat]
+    c = (0.5 * (nx - 1), 0.5 * (ny - 1), 0.5 * (nz - 1))
+    rho = tanh_ball(nx, ny, nz, *c, R, w, rl, rg)
+    if amp:
+        rho = rho + noise(seed, rho.shape, amp)
+    T = tanh_ball(nx, ny, nz, *c, R, w, T_sat * TC, T_wall * TC)
+    return Case3("heated_droplet3d_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, p or params(),
+                 wall_bc3(T_wall * TC, T_wall * TC), rho, T, steps, rl, rg)
+
+
+def sessile3d(nx=48, ny=48, nz=32, R=12.0, theta=90.0, w=4.0, Tr=0.86, amp=1e-4, seed=10,
+              steps=0, p=None) -> Case3:
+    """Spherical cap meeting the bottom wall line z = -1/2 at `theta`, walls at
+    both z ends held at Tr T_c."""
+    rg, rl = COEXISTENCE[Tr]
+    zc = -0.5 - R * np.cos(np.radians(theta))
+    rho = tanh_ball(nx, ny, nz, 0.5 * (nx - 1), 0.5 * (ny - 1), zc, R, w, rl, rg)
+    if amp:
+        rho = rho + noise(seed, rho.shape, amp)
+    T = np.full(rho.shape, Tr * TC)
+    bc = wall_bc3(Tr * TC, Tr * TC, theta_deg=theta)
+    return Case3("sessile3d_%g" % theta, nx, ny, nz, p or params(), bc, rho, T, steps, rl, rg,
+                 sessile=True)
