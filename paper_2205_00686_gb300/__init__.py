@@ -39,6 +39,10 @@ ABI_FUNCTIONS = (
     "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy", "lbm_set_tile", "lbm_get_tile",
     "lbm_autotune", "lbm_diag_reduce_noalloc", "lbm_reconfigure", "lbm_contact_angle",
     "lbm_regions",
+    # include/lbm3d.h
+    "lbm3d_state_bytes", "lbm3d_create", "lbm3d_init_fields", "lbm3d_step", "lbm3d_get_fields",
+    "lbm3d_get_populations", "lbm3d_diagnostics", "lbm3d_step_count", "lbm3d_sync",
+    "lbm3d_destroy", "lbm3d_last_error",
 )
 
 
@@ -73,6 +77,11 @@ class lbm_contact(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "theta_deg", "xc", "yc", "radius", "base_width", "height")] + [
         ("n_points", ctypes.c_int)]
+
+
+class lbm3d_bc(ctypes.Structure):
+    _fields_ = [("flow_z", ctypes.c_int), ("therm", ctypes.c_int * 2),
+                ("T_edge", ctypes.c_double * 2), ("theta_deg", ctypes.c_double)]
 
 
 class lbm_region(ctypes.Structure):
@@ -135,6 +144,20 @@ def lib():
             "lbm_regions": ([_vp, ctypes.c_double, ctypes.c_int, _vp,
                              ctypes.POINTER(lbm_region), ctypes.c_int,
                              ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "lbm3d_state_bytes": ([ctypes.c_int] * 4, ctypes.c_size_t),
+            "lbm3d_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                              ctypes.POINTER(lbm3d_bc), ctypes.c_int, _vp, ctypes.POINTER(_vp)],
+                             ctypes.c_int),
+            "lbm3d_init_fields": ([_vp] * 6, ctypes.c_int),
+            "lbm3d_step": ([_vp, ctypes.c_int], ctypes.c_int),
+            "lbm3d_get_fields": ([_vp] * 6, ctypes.c_int),
+            "lbm3d_get_populations": ([_vp] * 4, ctypes.c_int),
+            "lbm3d_diagnostics": ([_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, D],
+                                  ctypes.c_int),
+            "lbm3d_step_count": ([_vp], ctypes.c_longlong),
+            "lbm3d_sync": ([_vp], ctypes.c_int),
+            "lbm3d_destroy": ([_vp], None),
+            "lbm3d_last_error": ([_vp], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -319,6 +342,85 @@ class Domain:
         _check(lib().lbm_regions(self._h, float(threshold), int(bool(below)), None, None, 0,
                                  ctypes.byref(n)), self._h)
         return n.value
+
+
+def _check3(rc, ctx):
+    if rc != LBM_OK:
+        raise LbmError(rc, lib().lbm3d_last_error(ctx).decode() if ctx else "")
+    return rc
+
+
+def lbm3d_state_bytes(nx: int, ny: int, nz: int, prec) -> int:
+    return int(lib().lbm3d_state_bytes(nx, ny, nz, PRECISIONS.get(prec, prec)))
+
+
+class Domain3:
+    """One three-dimensional simulation context (``lbm3d_ctx``); host fields
+    are float64 arrays [nz][ny][nx]."""
+
+    def __init__(self, nx: int, ny: int, nz: int, params: dict, bc3: dict, prec="fp32",
+                 stream=None):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.prec = PRECISIONS.get(prec, prec)
+        self._p = make_params(params)
+        b = lbm3d_bc()
+        b.flow_z = int(bc3["flow_z"])
+        for e in range(2):
+            b.therm[e] = int(bc3["therm"][e])
+            b.T_edge[e] = float(bc3.get("T_edge", (0.0, 0.0))[e])
+        b.theta_deg = float(bc3.get("theta_deg", 90.0))
+        self._b = b
+        h = _vp()
+        _check(lib().lbm3d_create(self.nx, self.ny, self.nz, ctypes.byref(self._p),
+                                  ctypes.byref(self._b), self.prec, stream, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm3d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    def init_fields(self, rho, ux, uy, uz, T):
+        arrs = [a if hasattr(a, "data_ptr") else np.ascontiguousarray(a, np.float64)
+                for a in (rho, ux, uy, uz, T)]
+        _check3(lib().lbm3d_init_fields(self._h, *[_ptr(a) for a in arrs]), self._h)
+
+    def step(self, n: int = 1):
+        _check3(lib().lbm3d_step(self._h, int(n)), self._h)
+
+    def sync(self):
+        return _check3(lib().lbm3d_sync(self._h), self._h)
+
+    def get_fields(self, out=None):
+        out = out or tuple(np.empty(self._shape()) for _ in range(5))
+        _check3(lib().lbm3d_get_fields(self._h, *[_ptr(a) for a in out]), self._h)
+        return out
+
+    def populations(self):
+        f = np.empty((19,) + self._shape())
+        g = np.empty((7,) + self._shape())
+        P = np.empty(self._shape())
+        _check3(lib().lbm3d_get_populations(self._h, _ptr(f), _ptr(g), _ptr(P)), self._h)
+        return f, g, P
+
+    def diagnostics(self, rho_l, rho_g, sessile=False) -> dict:
+        d = lbm_diag()
+        _check3(lib().lbm3d_diagnostics(self._h, rho_l, rho_g, int(sessile), ctypes.byref(d)),
+                self._h)
+        return {k: getattr(d, k) for k, _ in lbm_diag._fields_}
+
+    @property
+    def step_count(self) -> int:
+        return int(lib().lbm3d_step_count(self._h))
 
 
 def lbm_diag_reduce_noalloc(rho, ux, uy, T, n, cv, rho_l, rho_g, out7, stream=None) -> int:

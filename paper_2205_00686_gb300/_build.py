@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblbm_gb300.so")
-SOURCES = ["lbm_step.cu", "lbm_aux.cu", "lbm_abi.cu", "lbm_noalloc.cu", "lbm_analysis.cu"]
+SOURCES = ["lbm_step.cu", "lbm_aux.cu", "lbm_abi.cu", "lbm_noalloc.cu", "lbm_analysis.cu", "lbm3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

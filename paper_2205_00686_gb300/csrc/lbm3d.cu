@@ -1,0 +1,930 @@
+// Three-dimensional form of the coupled step: D3Q19 MRT pseudopotential flow
+// lattice (d'Humieres moment basis, Li forcing with the sigma term on the
+// energy moment) + D3Q7 temperature lattice with the rho c_v-weighted
+// streaming of Eq. 39, x and y periodic, z periodic or walls.
+//
+// One step is three kernels over the nodes (plus a one-thread counter
+// update), because every stage needs neighbours of the previous one and a
+// fused sweep with recomputed halos does not fit shared memory in 3-D:
+//   k3_force    psi of the 18 neighbours (ghost layer at walls) -> F_m, F,
+//               u = (j + F/2)/rho, |F_m|^2/psi^2               (Eqs. 9, 11)
+//   k3_collide  div u (neighbour u), grad T (local moments), Q, P^n, S;
+//               D3Q19 and D3Q7 collisions; f* pushed to its destination
+//               (bounce-back at walls); g* and P^n stored    (Eqs. 5, 20, 24, 39)
+//   k3_blend    g(t+1) = g + (g*(y - c) - g)/(rho c_v) pulled (anti-bounce-back
+//               at walls); then rho, j, T, psi, T dp/dT of the new state
+//               from f(t+1) and g(t+1), and the density sum for buoyancy
+// Per node and step (FP32) this moves about 510 B against the 216 B of one
+// read and one write of the state; the design notes give the accounting.
+//
+// Populations are stored as deviations f_i - w_i rho_ref and g_i - w^_i T_ref.
+// Planes are [q][nz][ny][pitch], 64-bit offsets.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "lbm.h"
+#include "lbm3d.h"
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+// ---- D3Q19 / D3Q7 tables as constexpr functions (folded after unrolling) --
+__host__ __device__ constexpr int qx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int qy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+           : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int qz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+           : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int qopp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr int qc2(int i) { return qx(i) * qx(i) + qy(i) * qy(i) + qz(i) * qz(i); }
+__host__ __device__ constexpr double qw(int i) {
+    return qc2(i) == 0 ? 1.0 / 3.0 : (qc2(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+// moment k of direction i (d'Humieres et al. 2002 basis), integer valued
+__host__ __device__ constexpr int mrow(int k, int i) {
+    return k == 0 ? 1
+         : k == 1 ? 19 * qc2(i) - 30
+         : k == 2 ? (21 * qc2(i) * qc2(i) - 53 * qc2(i) + 24) / 2
+         : k == 3 ? qx(i)
+         : k == 4 ? (5 * qc2(i) - 9) * qx(i)
+         : k == 5 ? qy(i)
+         : k == 6 ? (5 * qc2(i) - 9) * qy(i)
+         : k == 7 ? qz(i)
+         : k == 8 ? (5 * qc2(i) - 9) * qz(i)
+         : k == 9 ? 3 * qx(i) * qx(i) - qc2(i)
+         : k == 10 ? (3 * qc2(i) - 5) * (3 * qx(i) * qx(i) - qc2(i))
+         : k == 11 ? qy(i) * qy(i) - qz(i) * qz(i)
+         : k == 12 ? (3 * qc2(i) - 5) * (qy(i) * qy(i) - qz(i) * qz(i))
+         : k == 13 ? qx(i) * qy(i)
+         : k == 14 ? qy(i) * qz(i)
+         : k == 15 ? qx(i) * qz(i)
+         : k == 16 ? (qy(i) * qy(i) - qz(i) * qz(i)) * qx(i)
+         : k == 17 ? (qz(i) * qz(i) - qx(i) * qx(i)) * qy(i)
+                   : (qx(i) * qx(i) - qy(i) * qy(i)) * qz(i);
+}
+// squared norm of row k (the basis is orthogonal: M^-1 = M^T diag(1/norm))
+__host__ __device__ constexpr int mnorm(int k) {
+    int s = 0;
+    for (int i = 0; i < 19; ++i) s += mrow(k, i) * mrow(k, i);
+    return s;
+}
+// D3Q7: rest, +-x, +-y, +-z
+__host__ __device__ constexpr int hx(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
+__host__ __device__ constexpr int hy(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }
+__host__ __device__ constexpr int hz(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
+
+enum { A_RHO = 0, A_T, A_PSI, A_TDPDT, A_JX, A_JY, A_JZ, A_N };   // aux planes
+enum { B_UX = 0, B_UY, B_UZ, B_FX, B_FY, B_FZ, B_FM2, B_N };      // aux2 planes
+
+struct Dom3 {
+    void* f[2];
+    void* g[2];
+    void* P[2];
+    void* gstar;
+    void* aux;
+    void* aux2;
+    Ctl* ctl;
+    int nx, ny, nz, pitch;
+    size_t plane;
+    int walls, therm[2];
+    double T_edge[2], cot, rho_ref, T_ref, inv_n;
+};
+
+template <class R>
+struct Lat3 {
+    R s_e, s_eps, s_q, s_p;
+    R sig_e3;            // (19/2) sigma / (1/s_e - 1/2), the sigma term of e
+    R vs0, vs1, vs3, vs4, w7_0, w7_1, cs2h, cv, gravity;
+    int frozen_flow, frozen_thermal;
+};
+
+template <class R>
+Lat3<R> make_lat3(const lbm_params& p) {
+    Lat3<R> L;
+    L.s_e = (R)p.s_e;
+    L.s_eps = (R)p.s_eps;
+    L.s_q = (R)p.s_q;
+    L.s_p = (R)(1.0 / (3.0 * p.nu + 0.5));
+    L.sig_e3 = (R)(9.5 * p.sigma / (1.0 / p.s_e - 0.5));
+    const double cs2h = p.w_dot / 3.0;
+    L.cs2h = (R)cs2h;
+    L.vs0 = (R)p.vs0;
+    L.vs1 = (R)(1.0 / (p.lambda / cs2h + 0.5));
+    L.vs3 = (R)p.vs3;
+    L.vs4 = (R)p.vs4;
+    L.w7_0 = (R)(1.0 - p.w_dot);
+    L.w7_1 = (R)(p.w_dot / 6.0);
+    L.cv = (R)p.cv;
+    L.gravity = (R)p.gravity;
+    L.frozen_flow = p.frozen_flow;
+    L.frozen_thermal = p.frozen_thermal;
+    return L;
+}
+
+// the EOS / interaction constants shared with the two-dimensional kernels
+PhysD phys_of(const lbm_params& p) {
+    PhysD d;
+    memset(&d, 0, sizeof(d));
+    d.a = p.a;
+    d.b = p.b;
+    d.Rg = p.R;
+    d.omega = p.omega;
+    d.G = p.G;
+    d.sigma = p.sigma;
+    d.s_e = p.s_e;
+    d.s_eps = p.s_eps;
+    d.s_q = p.s_q;
+    d.s_p = 1.0 / (3.0 * p.nu + 0.5);
+    d.cv = p.cv;
+    d.w_dot = p.w_dot;
+    d.vs1 = 1.0 / (p.lambda / (p.w_dot / 3.0) + 0.5);
+    d.vs3 = p.vs3;
+    d.vs4 = p.vs4;
+    d.gravity = p.gravity;
+    d.frozen_flow = p.frozen_flow;
+    d.frozen_thermal = p.frozen_thermal;
+    return d;
+}
+
+__device__ __forceinline__ int wrapn(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <class R>
+__device__ __forceinline__ size_t nid(const Dom3& D, int x, int y, int z) {
+    return ((size_t)z * D.ny + y) * D.pitch + x;
+}
+
+// ---------------------------------------------------------------------------
+// psi of a node at most one layer beyond the domain: z wraps or, at walls,
+// comes from the ghost layer built from rho / T of layers 1 and 2
+template <class R>
+__device__ R psi_nb(const Dom3& D, const Phys<R>& P, int x, int y, int z, int* err) {
+    const R* A = (const R*)D.aux;
+    x = wrapn(x, D.nx);
+    y = wrapn(y, D.ny);
+    if (z >= 0 && z < D.nz) return A[A_PSI * D.plane + nid<R>(D, x, y, z)];
+    if (!D.walls) return A[A_PSI * D.plane + nid<R>(D, x, y, wrapn(z, D.nz))];
+    const int e = z < 0 ? 0 : 1;
+    const int z1 = e == 0 ? 0 : D.nz - 1, z2 = e == 0 ? 1 : D.nz - 2;
+    const R* rho = A + A_RHO * D.plane;
+    const R dx = rho[nid<R>(D, wrapn(x + 1, D.nx), y, z1)] - rho[nid<R>(D, wrapn(x - 1, D.nx), y, z1)];
+    const R dy = rho[nid<R>(D, x, wrapn(y + 1, D.ny), z1)] - rho[nid<R>(D, x, wrapn(y - 1, D.ny), z1)];
+    const R rg = rho[nid<R>(D, x, y, z2)] + (R)D.cot * rsq(dx * dx + dy * dy);
+    const R tg = D.therm[e] == T_DIRICHLET ? (R)D.T_edge[e] : A[A_T * D.plane + nid<R>(D, x, y, z1)];
+    const R q2 = psi2_of(P, rg, tg);
+    if (!(q2 >= R(0))) *err |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
+    return f_sqrt(q2);
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) k3_force(Dom3 D, Phys<R> P, Lat3<R> L) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= D.nx || y >= D.ny) return;
+    const R* A = (const R*)D.aux;
+    R* B = (R*)D.aux2;
+    const size_t n = nid<R>(D, x, y, z);
+    int err = 0;
+    R sx = 0, sy = 0, sz = 0;
+#pragma unroll 19
+    for (int i = 1; i < 19; ++i) {
+        const R wv = qc2(i) == 1 ? R(1.0 / 6.0) : R(1.0 / 12.0);
+        const R pn = psi_nb<R>(D, P, x + qx(i), y + qy(i), z + qz(i), &err);
+        if (qx(i)) sx += wv * pn * R(qx(i));
+        if (qy(i)) sy += wv * pn * R(qy(i));
+        if (qz(i)) sz += wv * pn * R(qz(i));
+    }
+    const R psi = A[A_PSI * D.plane + n];
+    const R rho = A[A_RHO * D.plane + n];
+    const long long step = __ldcg(&D.ctl->step);
+    const R rho_ave = L.gravity != R(0) ? (R)(__ldcg(&D.ctl->mass[(step + 2) % 3]) * D.inv_n) : R(0);
+    const R Fx = P.negG * psi * sx, Fy = P.negG * psi * sy;
+    const R Fz = P.negG * psi * sz - L.gravity * (rho - rho_ave);
+    R ux = 0, uy = 0, uz = 0;
+    if (!L.frozen_flow) {
+        const R ir = R(1) / rho;
+        ux = (A[A_JX * D.plane + n] + R(0.5) * Fx) * ir;
+        uy = (A[A_JY * D.plane + n] + R(0.5) * Fy) * ir;
+        uz = (A[A_JZ * D.plane + n] + R(0.5) * Fz) * ir;
+    }
+    B[B_UX * D.plane + n] = ux;
+    B[B_UY * D.plane + n] = uy;
+    B[B_UZ * D.plane + n] = uz;
+    B[B_FX * D.plane + n] = Fx;
+    B[B_FY * D.plane + n] = Fy;
+    B[B_FZ * D.plane + n] = Fz;
+    B[B_FM2 * D.plane + n] = P.negG * P.negG * (sx * sx + sy * sy + sz * sz);
+    if (err) atomicOr(&D.ctl->err, err);
+}
+
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= D.nx || y >= D.ny) return;
+    const long long step = __ldcg(&D.ctl->step);
+    const int par = (int)(step & 1);
+    const R* fc = (const R*)D.f[par];
+    R* fn = (R*)D.f[par ^ 1];
+    const R* gc = (const R*)D.g[par];
+    const R* Pc = (const R*)D.P[par];
+    R* Pn_out = (R*)D.P[par ^ 1];
+    R* gs = (R*)D.gstar;
+    const R* A = (const R*)D.aux;
+    const R* B = (const R*)D.aux2;
+    const size_t n = nid<R>(D, x, y, z);
+    const R rho = A[A_RHO * D.plane + n];
+    const R T = A[A_T * D.plane + n];
+    const R TdpdT = A[A_TDPDT * D.plane + n];
+    const R ux = B[B_UX * D.plane + n], uy = B[B_UY * D.plane + n], uz = B[B_UZ * D.plane + n];
+    const R Fx = B[B_FX * D.plane + n], Fy = B[B_FY * D.plane + n], Fz = B[B_FZ * D.plane + n];
+    const R Fm2 = B[B_FM2 * D.plane + n];
+    R g[7];
+#pragma unroll 19
+    for (int i = 0; i < 7; ++i) g[i] = gc[i * D.plane + n];
+
+    // div u: (1/c_s^2) sum_i w_i c_i . u(x + c_i); walls carry u = 0
+    R divu = 0;
+#pragma unroll 19
+    for (int i = 1; i < 19; ++i) {
+        const int zz = z + qz(i);
+        if (D.walls && (zz < 0 || zz >= D.nz)) continue;
+        const size_t m = nid<R>(D, wrapn(x + qx(i), D.nx), wrapn(y + qy(i), D.ny), wrapn(zz, D.nz));
+        R cu = 0;
+        if (qx(i)) cu += R(qx(i)) * B[B_UX * D.plane + m];
+        if (qy(i)) cu += R(qy(i)) * B[B_UY * D.plane + m];
+        if (qz(i)) cu += R(qz(i)) * B[B_UZ * D.plane + m];
+        divu += R(3.0 * qw(i)) * cu;
+    }
+    // grad T from the local first moments: c^_s^2 d_a T = -vs1 m^_a
+    const R m1 = g[1] - g[2], m2 = g[3] - g[4], m3 = g[5] - g[6];
+    const R k = -L.vs1 / L.cs2h;
+    const R dTx = k * m1, dTy = k * m2, dTz = k * m3;
+    const R C = rho * L.cv;
+    const R Q = -(C * (ux * dTx + uy * dTy + uz * dTz) + TdpdT * divu);
+    const R Pn = Q / C;
+    const R Qs = step == 0 ? Q : Q + R(0.5) * (Q - C * Pc[n]);
+
+    // ---- D3Q19 MRT collision in moment space
+    R f[19];
+#pragma unroll 19
+    for (int i = 0; i < 19; ++i) f[i] = fc[i * D.plane + n];
+    if (L.frozen_flow) {
+#pragma unroll 19
+        for (int i = 0; i < 19; ++i) fn[i * D.plane + n] = f[i];
+    } else {
+        R m[19];
+#pragma unroll 19
+        for (int kk = 0; kk < 19; ++kk) {
+            R s = 0;
+#pragma unroll 19
+            for (int i = 0; i < 19; ++i)
+                if (mrow(kk, i)) s += R(mrow(kk, i)) * f[i];
+            m[kk] = s;
+        }
+        // deviation storage: m(abs) = m(dev) + rho_ref M w, M w = (1, -11, 3, 0 ...)
+        const R rr = (R)D.rho_ref;
+        m[0] += rr;
+        m[1] += R(-11) * rr;
+        m[2] += R(3) * rr;
+        const R uu = ux * ux + uy * uy + uz * uz;
+        const R uF = ux * Fx + uy * Fy + uz * Fz;
+        // equilibria (d'Humieres: w_eps = 3, w_epsj = -11/2, w_xx = -1/2)
+        R meq[19], Fb[19], sk[19];
+        meq[0] = rho;                            Fb[0] = 0;                  sk[0] = 0;
+        meq[1] = rho * (R(-11) + R(19) * uu);    Fb[1] = R(38) * uF + L.sig_e3 * Fm2;  sk[1] = L.s_e;
+        meq[2] = rho * (R(3) - R(5.5) * uu);     Fb[2] = R(-11) * uF;        sk[2] = L.s_eps;
+        meq[3] = rho * ux;                       Fb[3] = Fx;                 sk[3] = 1;
+        meq[4] = R(-2.0 / 3.0) * rho * ux;       Fb[4] = R(-2.0 / 3.0) * Fx; sk[4] = L.s_q;
+        meq[5] = rho * uy;                       Fb[5] = Fy;                 sk[5] = 1;
+        meq[6] = R(-2.0 / 3.0) * rho * uy;       Fb[6] = R(-2.0 / 3.0) * Fy; sk[6] = L.s_q;
+        meq[7] = rho * uz;                       Fb[7] = Fz;                 sk[7] = 1;
+        meq[8] = R(-2.0 / 3.0) * rho * uz;       Fb[8] = R(-2.0 / 3.0) * Fz; sk[8] = L.s_q;
+        const R pxx = R(3) * ux * ux - uu, axx = R(2) * ux * Fx - uy * Fy - uz * Fz;
+        const R pww = uy * uy - uz * uz, aww = uy * Fy - uz * Fz;
+        meq[9] = rho * pxx;                      Fb[9] = R(2) * axx;         sk[9] = L.s_p;
+        meq[10] = R(-0.5) * rho * pxx;           Fb[10] = -axx;              sk[10] = L.s_q;
+        meq[11] = rho * pww;                     Fb[11] = R(2) * aww;        sk[11] = L.s_p;
+        meq[12] = R(-0.5) * rho * pww;           Fb[12] = -aww;              sk[12] = L.s_q;
+        meq[13] = rho * ux * uy;                 Fb[13] = ux * Fy + uy * Fx; sk[13] = L.s_p;
+        meq[14] = rho * uy * uz;                 Fb[14] = uy * Fz + uz * Fy; sk[14] = L.s_p;
+        meq[15] = rho * ux * uz;                 Fb[15] = ux * Fz + uz * Fx; sk[15] = L.s_p;
+        meq[16] = 0;                             Fb[16] = 0;                 sk[16] = L.s_q;
+        meq[17] = 0;                             Fb[17] = 0;                 sk[17] = L.s_q;
+        meq[18] = 0;                             Fb[18] = 0;                 sk[18] = L.s_q;
+        // dm = -S (m - m^eq) + (I - S/2) Fbar, scaled by 1/|row|^2
+        R dm[19];
+#pragma unroll 19
+        for (int kk = 0; kk < 19; ++kk)
+            dm[kk] = (-sk[kk] * (m[kk] - meq[kk]) + (R(1) - R(0.5) * sk[kk]) * Fb[kk]) *
+                     R(1.0 / mnorm(kk));
+        // f* = f + M^T dm, pushed to x + c_i (bounce-back through walls)
+#pragma unroll 19
+        for (int i = 0; i < 19; ++i) {
+            R v = f[i];
+#pragma unroll 19
+            for (int kk = 0; kk < 19; ++kk)
+                if (mrow(kk, i)) v += R(mrow(kk, i)) * dm[kk];
+            const int zz = z + qz(i);
+            if (D.walls && (zz < 0 || zz >= D.nz)) {
+                fn[qopp(i) * D.plane + n] = v;
+            } else {
+                fn[i * D.plane + nid<R>(D, wrapn(x + qx(i), D.nx), wrapn(y + qy(i), D.ny),
+                                        wrapn(zz, D.nz))] = v;
+            }
+        }
+    }
+
+    // ---- D3Q7 MRT collision (deviation form), closed-form inverse of the
+    // moment matrix (rows 1, c_x, c_y, c_z, |c|^2, c_x^2 - c_y^2, c_y^2 - c_z^2)
+    {
+        const R Td = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+        const R m4 = g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+        const R m5 = (g[1] + g[2]) - (g[3] + g[4]);
+        const R m6 = (g[3] + g[4]) - (g[5] + g[6]);
+        const R wd = L.w7_1 * R(6);
+        const R s0 = Td - L.vs0 * (Td - Td) + Qs;
+        const R s1 = m1 - L.vs1 * m1, s2 = m2 - L.vs1 * m2, s3 = m3 - L.vs1 * m3;
+        const R s4 = m4 - L.vs3 * (m4 - wd * Td) + wd * Qs;
+        const R s5 = m5 - L.vs4 * m5, s6 = m6 - L.vs4 * m6;
+        const R b = (s4 - s5 + s6) * R(1.0 / 3.0);
+        const R a = b + s5, c = b - s6;
+        gs[0 * D.plane + n] = s0 - s4;
+        gs[1 * D.plane + n] = R(0.5) * (a + s1);
+        gs[2 * D.plane + n] = R(0.5) * (a - s1);
+        gs[3 * D.plane + n] = R(0.5) * (b + s2);
+        gs[4 * D.plane + n] = R(0.5) * (b - s2);
+        gs[5 * D.plane + n] = R(0.5) * (c + s3);
+        gs[6 * D.plane + n] = R(0.5) * (c - s3);
+    }
+    Pn_out[n] = Pn;
+    (void)T;
+}
+
+// ---------------------------------------------------------------------------
+// macroscopic fields of a node from its (deviation) populations
+template <class R>
+__device__ __forceinline__ void macro_node(const Dom3& D, const Phys<R>& P, const R* f19,
+                                           const R* g7, size_t n, int* err, R* rho_out) {
+    R* A = (R*)D.aux;
+    R rd = 0, jx = 0, jy = 0, jz = 0, Td = 0;
+#pragma unroll 19
+    for (int i = 0; i < 19; ++i) {
+        rd += f19[i];
+        if (qx(i)) jx += R(qx(i)) * f19[i];
+        if (qy(i)) jy += R(qy(i)) * f19[i];
+        if (qz(i)) jz += R(qz(i)) * f19[i];
+    }
+#pragma unroll 19
+    for (int i = 0; i < 7; ++i) Td += g7[i];
+    const R rho = rd + (R)D.rho_ref, T = Td + (R)D.T_ref;
+    R q2, TdpdT;
+    eos_node(P, rho, T, &q2, &TdpdT);
+    if (!(q2 >= R(0))) *err |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
+    if (!(T == T) || !(rho == rho)) *err |= ERR_NONFINITE;
+    A[A_RHO * D.plane + n] = rho;
+    A[A_T * D.plane + n] = T;
+    A[A_PSI * D.plane + n] = f_sqrt(q2);
+    A[A_TDPDT * D.plane + n] = TdpdT;
+    A[A_JX * D.plane + n] = jx;
+    A[A_JY * D.plane + n] = jy;
+    A[A_JZ * D.plane + n] = jz;
+    *rho_out = rho;
+}
+
+// block sum of rho into the density ring (FP64), for the buoyancy of the
+// next step
+__device__ __forceinline__ void add_mass(const Dom3& D, double v, int slot) {
+    __shared__ double red[4];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((t & 31) == 0) red[t >> 5] = v;
+    __syncthreads();
+    if (t == 0) atomicAdd(&D.ctl->mass[slot], red[0] + red[1] + red[2] + red[3]);
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) k3_blend(Dom3 D, Phys<R> P, Lat3<R> L, int use_mass) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool in = x < D.nx && y < D.ny;
+    double msum = 0.0;
+    const long long step = __ldcg(&D.ctl->step);
+    if (in) {
+        const int par = (int)(step & 1);
+        const R* gc = (const R*)D.g[par];
+        R* gn = (R*)D.g[par ^ 1];
+        const R* fn = (const R*)D.f[par ^ 1];
+        const R* gs = (const R*)D.gstar;
+        const R* A = (const R*)D.aux;
+        const size_t n = nid<R>(D, x, y, z);
+        const R iC = R(1) / (A[A_RHO * D.plane + n] * L.cv);
+        R g[7];
+#pragma unroll 19
+        for (int i = 0; i < 7; ++i) {
+            const R go = gc[i * D.plane + n];
+            if (L.frozen_thermal) {
+                g[i] = go;
+            } else {
+                const int zz = z - hz(i);
+                R Ai;
+                if (D.walls && (zz < 0 || zz >= D.nz)) {
+                    // i = 5 enters through the bottom, i = 6 through the top;
+                    // the outgoing partner is the opposite direction
+                    const int e = zz < 0 ? 0 : 1;
+                    const R gopp = gs[(i == 5 ? 6 : 5) * D.plane + n];
+                    Ai = D.therm[e] == T_DIRICHLET
+                             ? R(2) * L.w7_1 * (R)(D.T_edge[e] - D.T_ref) - gopp
+                             : gopp;
+                } else {
+                    Ai = gs[i * D.plane + nid<R>(D, wrapn(x - hx(i), D.nx), wrapn(y - hy(i), D.ny),
+                                                 wrapn(zz, D.nz))];
+                }
+                g[i] = go + (Ai - go) * iC;
+            }
+            gn[i * D.plane + n] = g[i];
+        }
+        R f[19];
+#pragma unroll 19
+        for (int i = 0; i < 19; ++i) f[i] = fn[i * D.plane + n];
+        int err = 0;
+        R rho;
+        macro_node<R>(D, P, f, g, n, &err, &rho);
+        if (err) atomicOr(&D.ctl->err, err);
+        msum = (double)rho;
+    }
+    if (use_mass) add_mass(D, in ? msum : 0.0, (int)((step + 1) % 3));
+}
+
+// macroscopic fields of the state at initialisation
+template <class R>
+__global__ void __launch_bounds__(128) k3_macro(Dom3 D, Phys<R> P, int use_mass, int slot) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool in = x < D.nx && y < D.ny;
+    double msum = 0.0;
+    if (in) {
+        const int par = (int)(__ldcg(&D.ctl->step) & 1);
+        const R* fc = (const R*)D.f[par];
+        const R* gc = (const R*)D.g[par];
+        const size_t n = nid<R>(D, x, y, z);
+        R f[19], g[7];
+#pragma unroll 19
+        for (int i = 0; i < 19; ++i) f[i] = fc[i * D.plane + n];
+#pragma unroll 19
+        for (int i = 0; i < 7; ++i) g[i] = gc[i * D.plane + n];
+        int err = 0;
+        R rho;
+        macro_node<R>(D, P, f, g, n, &err, &rho);
+        if (err) atomicOr(&D.ctl->err, err);
+        msum = (double)rho;
+    }
+    if (use_mass) add_mass(D, in ? msum : 0.0, slot);
+}
+
+// end of a step: advance the counter and clear the density slot that the
+// step after next accumulates into
+__global__ void k3_advance(Ctl* ctl) {
+    const long long s = ctl->step + 1;
+    ctl->step = s;
+    ctl->mass[(s + 1) % 3] = 0.0;
+}
+
+// populations f = f^eq(rho, u), g = w^ T as deviations; P = 0
+template <class R>
+__global__ void k3_init(Dom3 D, Lat3<R> L, const double* rho, const double* ux,
+                        const double* uy, const double* uz, const double* T) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= D.nx || y >= D.ny) return;
+    const size_t h = ((size_t)z * D.ny + y) * D.nx + x, n = nid<R>(D, x, y, z);
+    R* f = (R*)D.f[0];
+    R* g = (R*)D.g[0];
+    const double r = rho[h], a = ux[h], b = uy[h], c = uz[h], t = T[h];
+    const double uu = a * a + b * b + c * c;
+#pragma unroll 19
+    for (int i = 0; i < 19; ++i) {
+        const double cu = qx(i) * a + qy(i) * b + qz(i) * c;
+        const double fe = qw(i) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        f[i * D.plane + n] = (R)(fe - qw(i) * D.rho_ref);
+    }
+    const double w0 = (double)L.w7_0, w1 = (double)L.w7_1;
+#pragma unroll 19
+    for (int i = 0; i < 7; ++i) g[i * D.plane + n] = (R)((i == 0 ? w0 : w1) * (t - D.T_ref));
+    ((R*)D.P[0])[n] = R(0);
+}
+
+// state -> host-layout doubles: fields (rho, u, T) or absolute populations
+template <class R>
+__global__ void k3_export(Dom3 D, Lat3<R> L, int what, double* out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= D.nx || y >= D.ny) return;
+    const size_t N = (size_t)D.nx * D.ny * D.nz;
+    const size_t h = ((size_t)z * D.ny + y) * D.nx + x, n = nid<R>(D, x, y, z);
+    const int par = (int)(__ldcg(&D.ctl->step) & 1);
+    if (what == 0) {
+        const R* A = (const R*)D.aux;
+        const R* B = (const R*)D.aux2;
+        out[0 * N + h] = (double)A[A_RHO * D.plane + n];
+        out[1 * N + h] = (double)B[B_UX * D.plane + n];
+        out[2 * N + h] = (double)B[B_UY * D.plane + n];
+        out[3 * N + h] = (double)B[B_UZ * D.plane + n];
+        out[4 * N + h] = (double)A[A_T * D.plane + n];
+        const double ux = out[1 * N + h], uy = out[2 * N + h], uz = out[3 * N + h];
+        out[5 * N + h] = sqrt(ux * ux + uy * uy + uz * uz);
+    } else {
+        const R* f = (const R*)D.f[par];
+        const R* g = (const R*)D.g[par];
+        for (int i = 0; i < 19; ++i) out[i * N + h] = (double)f[i * D.plane + n] + qw(i) * D.rho_ref;
+        for (int i = 0; i < 7; ++i)
+            out[(19 + i) * N + h] = (double)g[i * D.plane + n] +
+                                    (double)(i == 0 ? L.w7_0 : L.w7_1) * D.T_ref;
+        out[26 * N + h] = (double)((const R*)D.P[par])[n];
+    }
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm3d_ctx {
+    int nx = 0, ny = 0, nz = 0, prec = 1;
+    lbm_params params;
+    lbm3d_bc bc;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* mem = nullptr;
+    Ctl* ctl = nullptr;
+    Dom3 D;
+    cudaGraphExec_t graph = nullptr;
+    long long step = 0;
+    bool initialized = false;
+    int sticky = LBM_OK;
+    std::string err;
+    double* host_buf = nullptr;   // device doubles: 27 N (export), reused
+    void* diag_scratch = nullptr;
+    double* diag_out = nullptr;
+    double* zeros = nullptr;
+};
+
+namespace {
+
+size_t pitch_for(int nx) { return ((size_t)nx + 31) / 32 * 32; }
+
+size_t bytes_for(int nx, int ny, int nz, int prec) {
+    const size_t es = prec == LBM_FP64 ? 8 : 4;
+    const size_t plane = pitch_for(nx) * ny * nz;
+    // f 2 x 19, g 2 x 7, g* 7, P 2, aux 7, aux2 7
+    return plane * es * (38 + 14 + 7 + 2 + A_N + B_N);
+}
+
+int set_err3(lbm3d_ctx* c, int code, const char* msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_err3(lbm3d_ctx* c, cudaError_t e, const char* where) {
+    if (e == cudaSuccess) return LBM_OK;
+    if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+}
+
+dim3 blk3() { return dim3(32, 4, 1); }
+dim3 grd3(const lbm3d_ctx* c) { return dim3((c->nx + 31) / 32, (c->ny + 3) / 4, c->nz); }
+
+template <class R>
+int launch_step(lbm3d_ctx* c) {
+    Phys<R> P = make_phys<R>(phys_of(c->params));
+    Lat3<R> L = make_lat3<R>(c->params);
+    const dim3 b = blk3(), g = grd3(c);
+    k3_force<R><<<g, b, 0, c->stream>>>(c->D, P, L);
+    k3_collide<R><<<g, b, 0, c->stream>>>(c->D, P, L);
+    k3_blend<R><<<g, b, 0, c->stream>>>(c->D, P, L, c->params.gravity != 0.0);
+    k3_advance<<<1, 1, 0, c->stream>>>(c->ctl);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int step_once(lbm3d_ctx* c) { return c->prec == LBM_FP64 ? launch_step<double>(c) : launch_step<float>(c); }
+
+int check3(lbm3d_ctx* c) {
+    Ctl h;
+    cudaError_t e = cudaMemcpyAsync(&h, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err3(c, e, "reading the control block");
+    if (h.err && c->sticky == LBM_OK) {
+        c->sticky = (h.err & ERR_PSI) ? LBM_EPSI : LBM_ENONFINITE;
+        c->err = c->sticky == LBM_EPSI ? "psi^2 < 0 at some node" : "non-finite density or temperature";
+    }
+    return c->sticky;
+}
+
+int ensure_buf(lbm3d_ctx* c) {
+    if (c->host_buf) return LBM_OK;
+    const size_t N = (size_t)c->nx * c->ny * c->nz;
+    cudaError_t e = cudaMalloc(&c->host_buf, 27 * N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->diag_scratch, diag_scratch_bytes((long long)N));
+    if (e == cudaSuccess) e = cudaMemset(c->diag_scratch, 0, diag_scratch_bytes((long long)N));
+    if (e == cudaSuccess) e = cudaMalloc(&c->diag_out, 16 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->zeros, N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(c->zeros, 0, N * sizeof(double));
+    return cuda_err3(c, e, "cudaMalloc(export buffers)");
+}
+
+// current fields (rho, u, T, |u|) into host_buf[0 .. 6N)
+int export_fields(lbm3d_ctx* c) {
+    int rc = ensure_buf(c);
+    if (rc) return rc;
+    const dim3 b = blk3(), g = grd3(c);
+    if (c->prec == LBM_FP64) {
+        k3_force<double><<<g, b, 0, c->stream>>>(c->D, make_phys<double>(phys_of(c->params)),
+                                                 make_lat3<double>(c->params));
+        k3_export<double><<<g, b, 0, c->stream>>>(c->D, make_lat3<double>(c->params), 0, c->host_buf);
+    } else {
+        k3_force<float><<<g, b, 0, c->stream>>>(c->D, make_phys<float>(phys_of(c->params)),
+                                                make_lat3<float>(c->params));
+        k3_export<float><<<g, b, 0, c->stream>>>(c->D, make_lat3<float>(c->params), 0, c->host_buf);
+    }
+    return cuda_err3(c, cudaGetLastError(), "field export");
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm3d_state_bytes(int nx, int ny, int nz, int prec) {
+    if (nx < 1 || ny < 1 || nz < 1 || (prec != LBM_FP64 && prec != LBM_FP32)) return 0;
+    return bytes_for(nx, ny, nz, prec);
+}
+
+int lbm3d_create(int nx, int ny, int nz, const lbm_params* params, const lbm3d_bc* bc, int prec,
+                 void* stream, lbm3d_ctx** out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !params || !bc || (prec != LBM_FP64 && prec != LBM_FP32))
+        return LBM_EINVAL;
+    if (nx > 65535 || ny > 65535 || nz > 65535) return LBM_EINVAL;
+    if (bc->flow_z != LBM_PERIODIC && bc->flow_z != LBM_WALL) return LBM_EINVAL;
+    for (int e = 0; e < 2; ++e) {
+        if (bc->therm[e] < 0 || bc->therm[e] > 2) return LBM_EINVAL;
+        if ((bc->flow_z == LBM_PERIODIC) != (bc->therm[e] == LBM_T_PERIODIC)) return LBM_EINVAL;
+    }
+    if (bc->flow_z == LBM_WALL && nz < 2) return LBM_EINVAL;
+    if (!(params->cv > 0) || !(params->nu > 0) || !(params->lambda > 0) ||
+        !(params->w_dot > 0 && params->w_dot < 1) || params->G == 0.0 || !(params->b > 0) ||
+        !(params->s_e > 0 && params->s_e < 2))
+        return LBM_EINVAL;
+    lbm3d_ctx* c = new (std::nothrow) lbm3d_ctx();
+    if (!c) return LBM_ENOMEM;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->prec = prec;
+    c->params = *params;
+    c->bc = *bc;
+    cudaError_t e = cudaSuccess;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        c->own_stream = e == cudaSuccess;
+    }
+    const size_t total = bytes_for(nx, ny, nz, prec);
+    if (e == cudaSuccess) e = cudaMalloc(&c->mem, total);
+    if (e == cudaSuccess) e = cudaMalloc(&c->ctl, sizeof(Ctl));
+    if (e == cudaSuccess) e = cudaMemset(c->ctl, 0, sizeof(Ctl));
+    if (e != cudaSuccess) {
+        const int rc = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+        lbm3d_destroy(c);
+        return rc;
+    }
+    const size_t es = prec == LBM_FP64 ? 8 : 4;
+    const size_t plane = pitch_for(nx) * ny * nz;
+    char* m = (char*)c->mem;
+    Dom3& D = c->D;
+    memset(&D, 0, sizeof(D));
+    size_t off = 0;
+    for (int p = 0; p < 2; ++p) { D.f[p] = m + off; off += 19 * plane * es; }
+    for (int p = 0; p < 2; ++p) { D.g[p] = m + off; off += 7 * plane * es; }
+    D.gstar = m + off; off += 7 * plane * es;
+    for (int p = 0; p < 2; ++p) { D.P[p] = m + off; off += plane * es; }
+    D.aux = m + off; off += A_N * plane * es;
+    D.aux2 = m + off;
+    D.ctl = c->ctl;
+    D.nx = nx;
+    D.ny = ny;
+    D.nz = nz;
+    D.pitch = (int)pitch_for(nx);
+    D.plane = plane;
+    D.walls = bc->flow_z == LBM_WALL;
+    D.therm[0] = bc->therm[0];
+    D.therm[1] = bc->therm[1];
+    D.T_edge[0] = bc->T_edge[0];
+    D.T_edge[1] = bc->T_edge[1];
+    D.cot = tan(M_PI / 2.0 - bc->theta_deg * M_PI / 180.0);
+    D.rho_ref = 1.0;
+    D.T_ref = 0.0;
+    D.inv_n = 1.0 / ((double)nx * ny * nz);
+    // the pitch padding is never read, but keep it defined
+    e = cudaMemset(c->mem, 0, total);
+    if (e != cudaSuccess) {
+        lbm3d_destroy(c);
+        return LBM_ECUDA;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm3d_init_fields(lbm3d_ctx* c, const double* rho, const double* ux, const double* uy,
+                      const double* uz, const double* T) {
+    if (!c || !rho || !ux || !uy || !uz || !T) return LBM_EINVAL;
+    const size_t N = (size_t)c->nx * c->ny * c->nz;
+    int rc = ensure_buf(c);
+    if (rc) return rc;
+    double sr = 0.0, sT = 0.0;
+    for (size_t n = 0; n < N; ++n) {
+        sr += rho[n];
+        sT += T[n];
+    }
+    c->D.rho_ref = c->params.rho_ref > 0 ? c->params.rho_ref : sr / (double)N;
+    c->D.T_ref = c->params.T_ref > 0 ? c->params.T_ref : sT / (double)N;
+    const double* src[5] = {rho, ux, uy, uz, T};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(c->host_buf + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice,
+                            c->stream);
+    Ctl h;
+    memset(&h, 0, sizeof(h));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_err3(c, e, "copying the initial fields");
+    const dim3 b = blk3(), g = grd3(c);
+    const int um = c->params.gravity != 0.0;
+    if (c->prec == LBM_FP64) {
+        k3_init<double><<<g, b, 0, c->stream>>>(c->D, make_lat3<double>(c->params), c->host_buf,
+                                                c->host_buf + N, c->host_buf + 2 * N,
+                                                c->host_buf + 3 * N, c->host_buf + 4 * N);
+        k3_macro<double><<<g, b, 0, c->stream>>>(c->D, make_phys<double>(phys_of(c->params)), um, 0);
+    } else {
+        k3_init<float><<<g, b, 0, c->stream>>>(c->D, make_lat3<float>(c->params), c->host_buf,
+                                               c->host_buf + N, c->host_buf + 2 * N,
+                                               c->host_buf + 3 * N, c->host_buf + 4 * N);
+        k3_macro<float><<<g, b, 0, c->stream>>>(c->D, make_phys<float>(phys_of(c->params)), um, 0);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err3(c, e, "init kernels");
+    // step 0 reads the initial density sum from slot 2 ((0 - 1) mod 3)
+    e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && um) {
+        double m0 = 0.0;
+        e = cudaMemcpy(&m0, &c->ctl->mass[0], sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&c->ctl->mass[2], &m0, sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return cuda_err3(c, e, "lbm3d_init_fields");
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;   // the launch arguments carry rho_ref / T_ref
+    c->step = 0;
+    c->sticky = LBM_OK;
+    c->initialized = true;
+    c->err.clear();
+    return check3(c);
+}
+
+int lbm3d_step(lbm3d_ctx* c, int n) {
+    if (!c || n < 0) return LBM_EINVAL;
+    if (!c->initialized) return set_err3(c, LBM_ESTATE, "lbm3d_step before lbm3d_init_fields");
+    if (c->sticky) return c->sticky;
+    const int kLen = 32;
+    int left = n;
+    if (left >= kLen) {
+        if (!c->graph) {
+            cudaGraph_t g;
+            cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_err3(c, e, "cudaStreamBeginCapture");
+            for (int i = 0; i < kLen; ++i) step_once(c);
+            e = cudaStreamEndCapture(c->stream, &g);
+            if (e != cudaSuccess) return cuda_err3(c, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                c->graph = nullptr;
+                return cuda_err3(c, e, "cudaGraphInstantiate");
+            }
+        }
+        for (; left >= kLen; left -= kLen) {
+            cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+            if (e != cudaSuccess) return cuda_err3(c, e, "cudaGraphLaunch");
+        }
+    }
+    for (; left > 0; --left)
+        if (step_once(c)) return cuda_err3(c, cudaGetLastError(), "step launch");
+    c->step += n;
+    return LBM_OK;
+}
+
+int lbm3d_get_fields(lbm3d_ctx* c, double* rho, double* ux, double* uy, double* uz, double* T) {
+    if (!c) return LBM_EINVAL;
+    if (!c->initialized) return set_err3(c, LBM_ESTATE, "no state yet");
+    int rc = export_fields(c);
+    if (rc) return rc;
+    const size_t N = (size_t)c->nx * c->ny * c->nz;
+    double* dst[5] = {rho, ux, uy, uz, T};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+        if (dst[k])
+            e = cudaMemcpyAsync(dst[k], c->host_buf + k * N, N * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream);
+    if (e != cudaSuccess) return cuda_err3(c, e, "copying fields to the host");
+    return check3(c);
+}
+
+int lbm3d_get_populations(lbm3d_ctx* c, double* f, double* g, double* P) {
+    if (!c) return LBM_EINVAL;
+    if (!c->initialized) return set_err3(c, LBM_ESTATE, "no state yet");
+    int rc = ensure_buf(c);
+    if (rc) return rc;
+    const size_t N = (size_t)c->nx * c->ny * c->nz;
+    const dim3 b = blk3(), gr = grd3(c);
+    if (c->prec == LBM_FP64)
+        k3_export<double><<<gr, b, 0, c->stream>>>(c->D, make_lat3<double>(c->params), 1, c->host_buf);
+    else
+        k3_export<float><<<gr, b, 0, c->stream>>>(c->D, make_lat3<float>(c->params), 1, c->host_buf);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && f)
+        e = cudaMemcpyAsync(f, c->host_buf, 19 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && g)
+        e = cudaMemcpyAsync(g, c->host_buf + 19 * N, 7 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && P)
+        e = cudaMemcpyAsync(P, c->host_buf + 26 * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_err3(c, e, "copying populations to the host");
+    return check3(c);
+}
+
+int lbm3d_diagnostics(lbm3d_ctx* c, double rho_l, double rho_g, int sessile, lbm_diag* out) {
+    if (!c || !out || !(rho_l > rho_g)) return LBM_EINVAL;
+    if (!c->initialized) return set_err3(c, LBM_ESTATE, "no state yet");
+    int rc = export_fields(c);
+    if (rc) return rc;
+    const size_t N = (size_t)c->nx * c->ny * c->nz;
+    // the reduction takes |u| in place of u_x and zeros for u_y
+    if (diag_launch(c->host_buf, c->host_buf + 5 * N, c->zeros, c->host_buf + 4 * N, (long long)N,
+                    c->params.cv, rho_l, rho_g, c->diag_out, c->diag_scratch, c->stream))
+        return cuda_err3(c, cudaGetLastError(), "diagnostics kernel");
+    double h[8];
+    cudaError_t e = cudaMemcpyAsync(h, c->diag_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err3(c, e, "diagnostics");
+    out->mass = h[0];
+    out->energy = h[1];
+    out->liquid_mass = h[2];
+    out->liquid_area = h[3];
+    out->liquid_area_smooth = h[4];
+    out->max_u = h[5];
+    out->nonfinite = (int)h[6];
+    const double fac = sessile ? 12.0 / M_PI : 6.0 / M_PI;
+    out->diameter = cbrt(fac * out->liquid_area);
+    out->diameter_smooth = cbrt(fac * out->liquid_area_smooth);
+    out->step = c->step;
+    return check3(c);
+}
+
+long long lbm3d_step_count(const lbm3d_ctx* c) { return c ? c->step : -1; }
+
+int lbm3d_sync(lbm3d_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    if (!c->initialized) return LBM_OK;
+    return check3(c);
+}
+
+void lbm3d_destroy(lbm3d_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->host_buf) cudaFree(c->host_buf);
+    if (c->diag_scratch) cudaFree(c->diag_scratch);
+    if (c->diag_out) cudaFree(c->diag_out);
+    if (c->zeros) cudaFree(c->zeros);
+    if (c->mem) cudaFree(c->mem);
+    if (c->ctl) cudaFree(c->ctl);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* lbm3d_last_error(const lbm3d_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads without a GPU and exports every
-symbol include/lbm.h declares (no compute calls here)."""
+symbol include/*.h declares (no compute calls here)."""
 import ctypes
 import os
 import re
@@ -11,9 +11,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(lbm_\w+)\s*\(", src, flags=re.M)
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(lbm\w*_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
@@ -30,7 +35,7 @@ def test_header_declares_the_abi():
     import paper_2205_00686_gb300 as lbm
     assert set(names) == set(lbm.ABI_FUNCTIONS)
     for core in ("lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_rho_u_T",
-                 "lbm_diagnostics"):
+                 "lbm_diagnostics", "lbm3d_create", "lbm3d_step"):
         assert core in names
 
 
@@ -48,3 +53,11 @@ def test_binding_loads_and_reports_sizes(built_lib):
     assert lbm.lbm_state_bytes(0, 10, "fp32") == 0
     p = lbm.make_params({})
     assert abs(p.sigma - 1.25) < 1e-15 and abs(p.cv - 5.0) < 1e-15
+
+
+def test_3d_state_bytes(built_lib):
+    import paper_2205_00686_gb300 as lbm
+    # 75 planes of [nz][ny][pitch] (pitch = nx rounded up to 32)
+    assert lbm.lbm3d_state_bytes(64, 48, 40, "fp32") == 75 * 64 * 48 * 40 * 4
+    assert lbm.lbm3d_state_bytes(33, 2, 3, "fp64") == 75 * 64 * 2 * 3 * 8
+    assert lbm.lbm3d_state_bytes(8, 8, 8, "fp32_g16") == 0
