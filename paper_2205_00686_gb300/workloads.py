@@ -334,3 +334,23 @@ def sessile3d(nx=48, ny=48, nz=32, R=12.0, theta=90.0, w=4.0, Tr=0.86, amp=1e-4,
     bc = wall_bc3(Tr * TC, Tr * TC, theta_deg=theta)
     return Case3("sessile3d_%g" % theta, nx, ny, nz, p or params(), bc, rho, T, steps, rl, rg,
                  sessile=True)
+
+
+def droplet_cloud3d(n=256, cells=4, R=None, w=4.0, Tr=0.86, amp=1e-4, seed=11, steps=1000,
+                    p=None) -> Case3:
+    """A periodic n^3 box tiled by cells^3 sub-cubes, each holding one droplet
+    at its centre (an evaporating spray's droplet cloud at T_sat).  R
+    defaults to a quarter of the sub-cube side."""
+    rg, rl = COEXISTENCE[Tr]
+    s = n // cells
+    R = 0.25 * s if R is None else R
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(np.float64)
+    # distance to the centre of the node's own sub-cube
+    c = 0.5 * (s - 1)
+    d = np.sqrt((np.mod(x, s) - c) ** 2 + (np.mod(y, s) - c) ** 2 + (np.mod(z, s) - c) ** 2)
+    rho = 0.5 * (rl + rg) - 0.5 * (rl - rg) * np.tanh((d - R) / (0.5 * w))
+    if amp:
+        rho = rho + noise(seed, rho.shape, amp)
+    T = np.full(rho.shape, Tr * TC)
+    return Case3("droplet_cloud3d_%d_%dx%dx%d" % (n, cells, cells, cells), n, n, n,
+                 p or params(), periodic_bc3(), rho, T, steps, rl, rg)
