@@ -163,6 +163,45 @@ __device__ __forceinline__ size_t nid(const Dom3& D, int x, int y, int z) {
     return ((size_t)z * D.ny + y) * D.pitch + x;
 }
 
+// Element offsets from a node to its six axis neighbours, wrapped across the
+// periodic seams; a lattice direction's offset is the sum of its components'.
+// zlo / zhi: the node is next to the bottom / top wall.
+struct Nbr {
+    long long xp, xm, yp, ym, zp, zm;
+    bool zlo, zhi;
+};
+
+__device__ __forceinline__ Nbr nbr_offsets(const Dom3& D, int x, int y, int z) {
+    Nbr d;
+    const long long P = D.pitch, S = (long long)D.ny * D.pitch;
+    d.xp = x == D.nx - 1 ? -(long long)(D.nx - 1) : 1;
+    d.xm = x == 0 ? (long long)(D.nx - 1) : -1;
+    d.yp = y == D.ny - 1 ? -(long long)(D.ny - 1) * P : P;
+    d.ym = y == 0 ? (long long)(D.ny - 1) * P : -P;
+    d.zp = z == D.nz - 1 ? -(long long)(D.nz - 1) * S : S;
+    d.zm = z == 0 ? (long long)(D.nz - 1) * S : -S;
+    d.zlo = D.walls && z == 0;
+    d.zhi = D.walls && z == D.nz - 1;
+    return d;
+}
+
+// offset of the node at c = (cx, cy, cz) away (each component -1, 0 or 1)
+__device__ __forceinline__ long long nbr_off(const Nbr& d, int cx, int cy, int cz) {
+    long long o = 0;
+    if (cx > 0) o += d.xp;
+    if (cx < 0) o += d.xm;
+    if (cy > 0) o += d.yp;
+    if (cy < 0) o += d.ym;
+    if (cz > 0) o += d.zp;
+    if (cz < 0) o += d.zm;
+    return o;
+}
+
+// the node c away lies beyond a wall
+__device__ __forceinline__ bool nbr_solid(const Nbr& d, int cz) {
+    return (cz < 0 && d.zlo) || (cz > 0 && d.zhi);
+}
+
 // ---------------------------------------------------------------------------
 // psi of a node at most one layer beyond the domain: z wraps or, at walls,
 // comes from the ghost layer built from rho / T of layers 1 and 2
@@ -194,17 +233,22 @@ __global__ void __launch_bounds__(128) k3_force(Dom3 D, Phys<R> P, Lat3<R> L) {
     const R* A = (const R*)D.aux;
     R* B = (R*)D.aux2;
     const size_t n = nid<R>(D, x, y, z);
+    const Nbr nb = nbr_offsets(D, x, y, z);
+    const R* psi_p = A + A_PSI * D.plane;
     int err = 0;
     R sx = 0, sy = 0, sz = 0;
 #pragma unroll 19
     for (int i = 1; i < 19; ++i) {
         const R wv = qc2(i) == 1 ? R(1.0 / 6.0) : R(1.0 / 12.0);
-        const R pn = psi_nb<R>(D, P, x + qx(i), y + qy(i), z + qz(i), &err);
+        // beyond a wall the neighbour is the ghost layer (Section 3.3)
+        const R pn = nbr_solid(nb, qz(i))
+                         ? psi_nb<R>(D, P, x + qx(i), y + qy(i), z + qz(i), &err)
+                         : psi_p[(size_t)((long long)n + nbr_off(nb, qx(i), qy(i), qz(i)))];
         if (qx(i)) sx += wv * pn * R(qx(i));
         if (qy(i)) sy += wv * pn * R(qy(i));
         if (qz(i)) sz += wv * pn * R(qz(i));
     }
-    const R psi = A[A_PSI * D.plane + n];
+    const R psi = psi_p[n];
     const R rho = A[A_RHO * D.plane + n];
     const long long step = __ldcg(&D.ctl->step);
     const R rho_ave = L.gravity != R(0) ? (R)(__ldcg(&D.ctl->mass[(step + 2) % 3]) * D.inv_n) : R(0);
@@ -246,7 +290,6 @@ __global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) 
     const R* B = (const R*)D.aux2;
     const size_t n = nid<R>(D, x, y, z);
     const R rho = A[A_RHO * D.plane + n];
-    const R T = A[A_T * D.plane + n];
     const R TdpdT = A[A_TDPDT * D.plane + n];
     const R ux = B[B_UX * D.plane + n], uy = B[B_UY * D.plane + n], uz = B[B_UZ * D.plane + n];
     const R Fx = B[B_FX * D.plane + n], Fy = B[B_FY * D.plane + n], Fz = B[B_FZ * D.plane + n];
@@ -255,13 +298,13 @@ __global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) 
 #pragma unroll 19
     for (int i = 0; i < 7; ++i) g[i] = gc[i * D.plane + n];
 
+    const Nbr nb = nbr_offsets(D, x, y, z);
     // div u: (1/c_s^2) sum_i w_i c_i . u(x + c_i); walls carry u = 0
     R divu = 0;
 #pragma unroll 19
     for (int i = 1; i < 19; ++i) {
-        const int zz = z + qz(i);
-        if (D.walls && (zz < 0 || zz >= D.nz)) continue;
-        const size_t m = nid<R>(D, wrapn(x + qx(i), D.nx), wrapn(y + qy(i), D.ny), wrapn(zz, D.nz));
+        if (nbr_solid(nb, qz(i))) continue;
+        const size_t m = (size_t)((long long)n + nbr_off(nb, qx(i), qy(i), qz(i)));
         R cu = 0;
         if (qx(i)) cu += R(qx(i)) * B[B_UX * D.plane + m];
         if (qy(i)) cu += R(qy(i)) * B[B_UY * D.plane + m];
@@ -337,13 +380,10 @@ __global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) 
 #pragma unroll 19
             for (int kk = 0; kk < 19; ++kk)
                 if (mrow(kk, i)) v += R(mrow(kk, i)) * dm[kk];
-            const int zz = z + qz(i);
-            if (D.walls && (zz < 0 || zz >= D.nz)) {
+            if (nbr_solid(nb, qz(i)))
                 fn[qopp(i) * D.plane + n] = v;
-            } else {
-                fn[i * D.plane + nid<R>(D, wrapn(x + qx(i), D.nx), wrapn(y + qy(i), D.ny),
-                                        wrapn(zz, D.nz))] = v;
-            }
+            else
+                fn[i * D.plane + (size_t)((long long)n + nbr_off(nb, qx(i), qy(i), qz(i)))] = v;
         }
     }
 
@@ -370,7 +410,6 @@ __global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) 
         gs[6 * D.plane + n] = R(0.5) * (c - s3);
     }
     Pn_out[n] = Pn;
-    (void)T;
 }
 
 // ---------------------------------------------------------------------------
@@ -431,6 +470,7 @@ __global__ void __launch_bounds__(128) k3_blend(Dom3 D, Phys<R> P, Lat3<R> L, in
         const R* gs = (const R*)D.gstar;
         const R* A = (const R*)D.aux;
         const size_t n = nid<R>(D, x, y, z);
+        const Nbr nb = nbr_offsets(D, x, y, z);
         const R iC = R(1) / (A[A_RHO * D.plane + n] * L.cv);
         R g[7];
 #pragma unroll 19
@@ -439,19 +479,17 @@ __global__ void __launch_bounds__(128) k3_blend(Dom3 D, Phys<R> P, Lat3<R> L, in
             if (L.frozen_thermal) {
                 g[i] = go;
             } else {
-                const int zz = z - hz(i);
                 R Ai;
-                if (D.walls && (zz < 0 || zz >= D.nz)) {
+                if (nbr_solid(nb, -hz(i))) {
                     // i = 5 enters through the bottom, i = 6 through the top;
                     // the outgoing partner is the opposite direction
-                    const int e = zz < 0 ? 0 : 1;
+                    const int e = i == 5 ? 0 : 1;
                     const R gopp = gs[(i == 5 ? 6 : 5) * D.plane + n];
                     Ai = D.therm[e] == T_DIRICHLET
                              ? R(2) * L.w7_1 * (R)(D.T_edge[e] - D.T_ref) - gopp
                              : gopp;
                 } else {
-                    Ai = gs[i * D.plane + nid<R>(D, wrapn(x - hx(i), D.nx), wrapn(y - hy(i), D.ny),
-                                                 wrapn(zz, D.nz))];
+                    Ai = gs[i * D.plane + (size_t)((long long)n + nbr_off(nb, -hx(i), -hy(i), -hz(i)))];
                 }
                 g[i] = go + (Ai - go) * iC;
             }
@@ -607,6 +645,7 @@ int cuda_err3(lbm3d_ctx* c, cudaError_t e, const char* where) {
     return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
 }
 
+// one thread per node
 dim3 blk3() { return dim3(32, 4, 1); }
 dim3 grd3(const lbm3d_ctx* c) { return dim3((c->nx + 31) / 32, (c->ny + 3) / 4, c->nz); }
 
@@ -655,11 +694,11 @@ int export_fields(lbm3d_ctx* c) {
     const dim3 b = blk3(), g = grd3(c);
     if (c->prec == LBM_FP64) {
         k3_force<double><<<g, b, 0, c->stream>>>(c->D, make_phys<double>(phys_of(c->params)),
-                                                 make_lat3<double>(c->params));
+                                                   make_lat3<double>(c->params));
         k3_export<double><<<g, b, 0, c->stream>>>(c->D, make_lat3<double>(c->params), 0, c->host_buf);
     } else {
         k3_force<float><<<g, b, 0, c->stream>>>(c->D, make_phys<float>(phys_of(c->params)),
-                                                make_lat3<float>(c->params));
+                                                  make_lat3<float>(c->params));
         k3_export<float><<<g, b, 0, c->stream>>>(c->D, make_lat3<float>(c->params), 0, c->host_buf);
     }
     return cuda_err3(c, cudaGetLastError(), "field export");
