@@ -14,8 +14,9 @@
 //   k3_blend    g(t+1) = g + (g*(y - c) - g)/(rho c_v) pulled (anti-bounce-back
 //               at walls); then rho, j, T, psi, T dp/dT of the new state
 //               from f(t+1) and g(t+1), and the density sum for buoyancy
-// Per node and step (FP32) this moves about 510 B against the 216 B of one
-// read and one write of the state; the design notes give the accounting.
+// Per node and step (FP32) this moves about twice the 216 B of one read and
+// one write of the state: f is read again after the push to build the next
+// state's rho, j and psi, and u, F pass through memory once.
 //
 // Populations are stored as deviations f_i - w_i rho_ref and g_i - w^_i T_ref.
 // Planes are [q][nz][ny][pitch], 64-bit offsets.
