@@ -798,18 +798,22 @@ int lbm3d_init_fields(lbm3d_ctx* c, const double* rho, const double* ux, const d
     const size_t N = (size_t)c->nx * c->ny * c->nz;
     int rc = ensure_buf(c);
     if (rc) return rc;
-    double sr = 0.0, sT = 0.0;
-    for (size_t n = 0; n < N; ++n) {
-        sr += rho[n];
-        sT += T[n];
-    }
-    c->D.rho_ref = c->params.rho_ref > 0 ? c->params.rho_ref : sr / (double)N;
-    c->D.T_ref = c->params.T_ref > 0 ? c->params.T_ref : sT / (double)N;
     const double* src[5] = {rho, ux, uy, uz, T};
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
         e = cudaMemcpyAsync(c->host_buf + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice,
                             c->stream);
+    // storage references from device sums (fixed summation order)
+    double sums[2];
+    if (e == cudaSuccess && sum2_launch(c->host_buf, c->host_buf + 4 * N, (long long)N,
+                                        c->diag_out + 8, c->diag_scratch, c->stream))
+        e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sums, c->diag_out + 8, sizeof(sums), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err3(c, e, "field sums");
+    c->D.rho_ref = c->params.rho_ref > 0 ? c->params.rho_ref : sums[0] / (double)N;
+    c->D.T_ref = c->params.T_ref > 0 ? c->params.T_ref : sums[1] / (double)N;
     Ctl h;
     memset(&h, 0, sizeof(h));
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream);

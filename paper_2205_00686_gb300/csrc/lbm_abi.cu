@@ -460,18 +460,23 @@ int lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, const doubl
     const size_t N = (size_t)c->nx * c->ny;
     int rc = ensure_fields(c);
     if (rc) return rc;
-    double sr = 0.0, sT = 0.0;
-    for (size_t n = 0; n < N; ++n) {
-        sr += rho[n];
-        sT += T[n];
-    }
-    c->inst.rho_ref = c->params.rho_ref > 0 ? c->params.rho_ref : sr / (double)N;
-    c->inst.T_ref = c->params.T_ref > 0 ? c->params.T_ref : sT / (double)N;
     const double* src[4] = {rho, ux, uy, T};
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         e = cudaMemcpyAsync(c->fields + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_err(c, e, "copying the initial fields");
+    // sum rho and sum T on the device (fixed summation order): the storage
+    // references and the first step's mean density
+    double sums[2];
+    if (sum2_launch(c->fields, c->fields + 3 * N, (long long)N, c->diag_out + 8, c->diag_scratch,
+                    c->stream))
+        return cuda_err(c, cudaGetLastError(), "field sums");
+    e = cudaMemcpyAsync(sums, c->diag_out + 8, sizeof(sums), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "field sums");
+    const double sr = sums[0], sT = sums[1];
+    c->inst.rho_ref = c->params.rho_ref > 0 ? c->params.rho_ref : sr / (double)N;
+    c->inst.T_ref = c->params.T_ref > 0 ? c->params.T_ref : sT / (double)N;
     if ((rc = ctx_upload_inst(c))) return rc;
     if (init_launch(c->prec, c->inst_dev, c->inst, c->fields, c->fields + N, c->fields + 2 * N,
                     c->fields + 3 * N, c->params.w_dot, c->stream))

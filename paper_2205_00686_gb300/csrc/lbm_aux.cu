@@ -28,16 +28,33 @@ __global__ void k_init(Inst I, const double* rho, const double* ux, const double
     const size_t plane = (size_t)I.ny * I.pitch;
     const size_t off = (size_t)y * I.pitch + x;
     const double r = rho[n], vx = ux[n], vy = uy[n], t = T[n];
-    const double uu = vx * vx + vy * vy;
     TF* f = (TF*)I.f[0];
     TG* g = (TG*)I.g[0];
     R* P = (R*)I.P[0];
-    for (int i = 0; i < 9; ++i) {
-        const double cu = dCX9[i] * vx + dCY9[i] * vy;
-        const double fe = dW9[i] * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-        st_st(f + i * plane + off, (TF)(fe - dW9[i] * I.rho_ref));
+    if (PREC == 0) {
+        const double uu = vx * vx + vy * vy;
+        for (int i = 0; i < 9; ++i) {
+            const double cu = dCX9[i] * vx + dCY9[i] * vy;
+            const double fe = dW9[i] * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+            st_st(f + i * plane + off, (TF)(fe - dW9[i] * I.rho_ref));
+        }
+        for (int i = 0; i < 5; ++i) st_st(g + i * plane + off, (R)(w5(i, w_dot) * (t - I.T_ref)));
+    } else {
+        // FP32 state: the deviation f^eq - w rho_ref = w [(rho - rho_ref) +
+        // rho (3 c.u + 9/2 (c.u)^2 - 3/2 u^2)] in float (the reference
+        // difference in double), which stays within the state's own rounding
+        const float dr = (float)(r - I.rho_ref), rf = (float)r;
+        const float fx = (float)vx, fy = (float)vy, uu = fx * fx + fy * fy;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float cu = (float)dCX9[i] * fx + (float)dCY9[i] * fy;
+            const float w = (float)dW9[i];
+            st_st(f + i * plane + off, (TF)(w * (dr + rf * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu))));
+        }
+        const float td = (float)(t - I.T_ref);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) st_st(g + i * plane + off, (float)w5(i, w_dot) * td);
     }
-    for (int i = 0; i < 5; ++i) st_st(g + i * plane + off, (R)(w5(i, w_dot) * (t - I.T_ref)));
     P[off] = R(0);
 }
 
@@ -92,9 +109,47 @@ __global__ void k_fields_node(Inst I, PhysD p, const Ctl* ctl, double* orho, dou
     opsi[n] = psi_of(p, r, t);
 }
 
+// FP32 state: the same fields from float sums of the stored deviations and
+// the float EOS (the state's own precision; the GPU's FP64 rate would
+// otherwise bound this pass)
+template <int PREC>
+__global__ void k_fields_node_f(Inst I, Phys<float> pf, const Ctl* ctl, double* orho,
+                                double* ojx, double* ojy, double* oT, double* opsi) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= I.nx) return;
+    const long long step = __ldcg(&ctl->step);
+    const int par = (int)(step & 1);
+    typedef typename Types<PREC>::TF TF;
+    typedef typename Types<PREC>::TG TG;
+    const TF* f = (const TF*)I.f[par];
+    const TG* g = (const TG*)I.g[par];
+    const size_t plane = (size_t)I.ny * I.pitch, off = (size_t)y * I.pitch + x;
+    float rd = 0.f, jx = 0.f, jy = 0.f, td = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float fi = (float)ld_st(f + i * plane + off);
+        rd += fi;
+        jx += (float)dCX9[i] * fi;
+        jy += (float)dCY9[i] * fi;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) td += (float)ld_st(g + i * plane + off);
+    // sum_i w_i = sum_i w^_i = 1 and sum_i w_i c_i = 0: the references add
+    // once to rho and T and not to j
+    const float r = rd + (float)I.rho_ref, t = td + (float)I.T_ref;
+    const size_t n = (size_t)y * I.nx + x;
+    orho[n] = r;
+    oT[n] = t;
+    ojx[n] = jx;
+    ojy[n] = jy;
+    opsi[n] = f_sqrt(psi2_of(pf, r, t));
+}
+
 // pass 2: F_m from the psi field (Eq. 9, wetting ghost layer of Section 3.3),
 // buoyancy, and u = (j + F/2) / rho (Eq. 11), in place over j
-__global__ void k_fields_force(Inst I, PhysD p, const Ctl* ctl, const double* rho,
+template <class C>
+__global__ void k_fields_force(Inst I, PhysD p, Phys<float> pf, const Ctl* ctl, const double* rho,
                                double* ux, double* uy, const double* T, const double* psi) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -102,9 +157,9 @@ __global__ void k_fields_force(Inst I, PhysD p, const Ctl* ctl, const double* rh
     const int nx = I.nx, ny = I.ny;
     const bool perx = I.flow[EW] == PERIODIC;
     auto extx = [&](int xx) { return perx ? wrapi(xx, nx) : min(max(xx, 0), nx - 1); };
-    auto at = [&](const double* a, int xx, int yy) { return a[(size_t)yy * nx + xx]; };
-    const double cot = I.cot_theta;
-    auto psi_ext = [&](int xx, int yy) -> double {
+    auto at = [&](const double* a, int xx, int yy) { return (C)a[(size_t)yy * nx + xx]; };
+    const C cot = (C)I.cot_theta;
+    auto psi_ext = [&](int xx, int yy) -> C {
         const int xe = extx(xx);
         if (yy >= 0 && yy < ny) return at(psi, xe, yy);
         const int edge = yy < 0 ? ES : EN;
@@ -112,35 +167,43 @@ __global__ void k_fields_force(Inst I, PhysD p, const Ctl* ctl, const double* rh
         if (kind == PERIODIC) return at(psi, xe, wrapi(yy, ny));
         if (kind == OPEN) return at(psi, xe, yy < 0 ? 0 : ny - 1);
         const int y1 = edge == ES ? 0 : ny - 1, y2 = edge == ES ? 1 : ny - 2;
-        const double rg = at(rho, xe, y2) + cot * fabs(at(rho, extx(xe + 1), y1) - at(rho, extx(xe - 1), y1));
-        const double tg = I.therm[edge] == T_DIRICHLET ? wall_T(I, edge, xe) : at(T, xe, y1);
-        return psi_of(p, rg, tg);
+        const C rg = at(rho, xe, y2) + cot * rabs(at(rho, extx(xe + 1), y1) - at(rho, extx(xe - 1), y1));
+        const C tg = I.therm[edge] == T_DIRICHLET ? (C)wall_T(I, edge, xe) : at(T, xe, y1);
+        if (sizeof(C) == 8) return (C)psi_of(p, (double)rg, (double)tg);
+        return (C)f_sqrt(psi2_of(pf, (float)rg, (float)tg));
     };
-    double sx = 0.0, sy = 0.0;
+    C sx = 0, sy = 0;
+#pragma unroll
     for (int i = 1; i < 9; ++i) {
-        const double wv = i < 5 ? 1.0 / 3.0 : 1.0 / 12.0;
-        const double pn = psi_ext(x + dCX9[i], y + dCY9[i]);
-        sx += wv * pn * dCX9[i];
-        sy += wv * pn * dCY9[i];
+        const C wv = i < 5 ? C(1.0 / 3.0) : C(1.0 / 12.0);
+        const C pn = psi_ext(x + dCX9[i], y + dCY9[i]);
+        sx += wv * pn * (C)dCX9[i];
+        sy += wv * pn * (C)dCY9[i];
     }
     const size_t n = (size_t)y * nx + x;
-    const double r = rho[n], pc = psi[n];
-    const double Fx = -p.G * pc * sx;
+    const C r = (C)rho[n], pc = (C)psi[n];
+    const C G = (C)p.G;
+    const C Fx = -G * pc * sx;
     const long long step = __ldcg(&ctl->step);
-    const double rho_ave = __ldcg(&ctl->mass[(step + 2) % 3]) * I.inv_n;
-    const double Fy = -p.G * pc * sy - (r - rho_ave) * p.gravity;
-    ux[n] = p.frozen_flow ? 0.0 : (ux[n] + 0.5 * Fx) / r;
-    uy[n] = p.frozen_flow ? 0.0 : (uy[n] + 0.5 * Fy) / r;
+    const C rho_ave = (C)(__ldcg(&ctl->mass[(step + 2) % 3]) * I.inv_n);
+    const C Fy = -G * pc * sy - (r - rho_ave) * (C)p.gravity;
+    ux[n] = p.frozen_flow ? 0.0 : (double)(((C)ux[n] + C(0.5) * Fx) / r);
+    uy[n] = p.frozen_flow ? 0.0 : (double)(((C)uy[n] + C(0.5) * Fy) / r);
 }
 
 int fields_launch(int prec, const Inst* I_dev, const Inst& I, const PhysD& phys, double* rho,
                   double* ux, double* uy, double* T, double* psi, cudaStream_t st) {
     (void)I_dev;
     dim3 blk(128), grd((I.nx + 127) / 128, I.ny);
-    if (prec == 0) k_fields_node<0><<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T, psi);
-    else if (prec == 1) k_fields_node<1><<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T, psi);
-    else k_fields_node<2><<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T, psi);
-    k_fields_force<<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T, psi);
+    const Phys<float> pf = make_phys<float>(phys);
+    if (prec == 0) {
+        k_fields_node<0><<<grd, blk, 0, st>>>(I, phys, I.ctl, rho, ux, uy, T, psi);
+        k_fields_force<double><<<grd, blk, 0, st>>>(I, phys, pf, I.ctl, rho, ux, uy, T, psi);
+    } else {
+        if (prec == 1) k_fields_node_f<1><<<grd, blk, 0, st>>>(I, pf, I.ctl, rho, ux, uy, T, psi);
+        else k_fields_node_f<2><<<grd, blk, 0, st>>>(I, pf, I.ctl, rho, ux, uy, T, psi);
+        k_fields_force<float><<<grd, blk, 0, st>>>(I, phys, pf, I.ctl, rho, ux, uy, T, psi);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -261,6 +324,57 @@ __global__ void __launch_bounds__(DIAG_THREADS)
         out[k] = x;
         if (k == 0) *ticket = 0u;
     }
+}
+
+// sum rho and sum T of device fields (the storage references and the first
+// step's mean density), with the same fixed-order two-level reduction
+__global__ void __launch_bounds__(DIAG_THREADS)
+    k_sum2(const double* a, const double* b, long long n, double* out, double* partial,
+           unsigned* ticket) {
+    __shared__ double red[2][DIAG_THREADS / 32];
+    __shared__ bool last;
+    double v0 = 0.0, v1 = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        v0 += a[i];
+        v1 += b[i];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, o);
+        v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    }
+    if (lane == 0) {
+        red[0][wid] = v0;
+        red[1][wid] = v1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int k = threadIdx.x;
+        double x = red[k][0];
+        for (int w = 1; w < DIAG_THREADS / 32; ++w) x += red[k][w];
+        partial[blockIdx.x * 2 + k] = x;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x < 2) {
+        __threadfence();
+        const int k = threadIdx.x;
+        double x = __ldcg(&partial[k]);
+        for (unsigned bk = 1; bk < gridDim.x; ++bk) x += __ldcg(&partial[bk * 2 + k]);
+        out[k] = x;
+        if (k == 0) *ticket = 0u;
+    }
+}
+
+int sum2_launch(const double* a, const double* b, long long n, double* out2, void* scratch,
+                cudaStream_t st) {
+    double* partial = (double*)scratch;
+    unsigned* ticket = (unsigned*)((char*)scratch + (size_t)DIAG_BLOCKS * DIAG_VALS * sizeof(double));
+    k_sum2<<<DIAG_BLOCKS, DIAG_THREADS, 0, st>>>(a, b, n, out2, partial, ticket);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int diag_launch(const double* rho, const double* ux, const double* uy, const double* T,

@@ -234,6 +234,10 @@ size_t diag_scratch_bytes(long long n);
 int diag_launch(const double* rho, const double* ux, const double* uy, const double* T,
                 long long n, double cv, double rho_l, double rho_g, double* out9,
                 void* scratch, cudaStream_t st);
+// out2 = (sum a, sum b) over n device doubles, fixed summation order; the
+// same scratch as diag_launch
+int sum2_launch(const double* a, const double* b, long long n, double* out2, void* scratch,
+                cudaStream_t st);
 
 // interface analyses (lbm_analysis.cu)
 // contact-angle sums: out12[0..8] = n, sum u, sum v, sum uu, sum vv, sum uv,
