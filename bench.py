@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--serve-steps", type=int, default=500)
     ap.add_argument("--size", type=int, default=NX,
                     help="domain side (default 4096; smaller sides for profiler captures)")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "fp32_g16"],
+                    help="precision of the timed domain (profiler captures; the metric is FP32)")
     ap.add_argument("--only-3d", type=int, default=0, metavar="N",
                     help="run only the 3-D leg on an N^3 droplet cloud (profiler captures)")
     return ap.parse_args()
@@ -283,7 +285,7 @@ def run_ours(args):
     case = make_case(args.size)
     N = case.nx * case.ny
 
-    dom = lbm.Domain(case.nx, case.ny, case.params, case.bc, prec="fp32",
+    dom = lbm.Domain(case.nx, case.ny, case.params, case.bc, prec=args.prec,
                      stream=stream.cuda_stream)
     if args.tile:
         dom.set_tile(*[int(v) for v in args.tile.split(",")])
@@ -324,19 +326,21 @@ def run_ours(args):
            "call": "lbm_init_fields(host) + lbm_step(%d) + lbm_get_rho_u_T(host)" % e2e_steps}
 
     peak, peak_kind = measured_peaks()
-    algo = BYTES_PER_NODE["fp32"] * N
+    algo = BYTES_PER_NODE[args.prec] * N
     achieved = algo / (t / args.steps) / 1e9   # per GPU: each rank steps its own domain
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as fh:
             tr = json.load(fh)
-        if tr.get("source_hash") == step_source_hash() and tr.get("prec") == "fp32":
+        if tr.get("source_hash") == step_source_hash() and tr.get("prec") == args.prec \
+                and case.nx == 4096 and case.ny == 4096:
             traffic = tr.get("bytes_per_launch_4096")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": "%s hbm_gbs (copy)" % peak_kind,
-                "algorithmic_bytes_per_node": BYTES_PER_NODE["fp32"],
-                "kernel": "lbm::k_step<1,%d>" % dom.tile()[0]}
+                "algorithmic_bytes_per_node": BYTES_PER_NODE[args.prec],
+                "kernel": "lbm::k_step<%d,%d>" % ({"fp64": 0, "fp32": 1, "fp32_g16": 2}[args.prec],
+                                                  dom.tile()[0])}
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -374,13 +378,15 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp32_g16": "f32 (g stored f16)"}[args.prec],
         "data": "synthetic",
         "config": {"workload": "droplet evaporation, open outflow, Dirichlet 0.95Tc edges, "
-                               "R=%g, %dx%d, FP32 fused step" % (640.0 * case.nx / 4096.0,
-                                                                  case.nx, case.ny),
+                               "R=%g, %dx%d, %s fused step" % (640.0 * case.nx / 4096.0,
+                                                               case.nx, case.ny, args.prec.upper()),
                    "nx": case.nx, "ny": case.ny,
-                   "l2": "inputs larger than L2 (%.2f GiB state)" % (2 * 60.0 * N / 2 ** 30),
+                   "l2": "inputs larger than L2 (%.2f GiB state)"
+                         % (BYTES_PER_NODE[args.prec] * N / 2 ** 30),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "tile": list(dom.tile())},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
