@@ -34,6 +34,11 @@ sys.path.insert(0, ROOT)
 
 NX = NY = 4096
 BYTES_PER_NODE = {"fp32": 120, "fp64": 240, "fp32_g16": 100}
+# FP64 FLOP per node update of the FP64 step (2 DFMA + DADD + DMUL thread
+# instructions per node, ncu on the same kernel: profiles/k_step_fp64_2048_alu.md)
+# and the nominal FP64 rate of the part (no measured FP64 peak on this machine)
+FP64_FLOP_PER_NODE = 368.0
+FP64_NOMINAL_GFLOPS = 1250.0
 METRIC = "coupled D2Q9+D2Q5 MLUPS and % of HBM roofline, FP32 vs FP64 at stated error"
 STEP_SOURCES = ["paper_2205_00686_gb300/csrc/lbm_step.cu",
                 "paper_2205_00686_gb300/csrc/lbm_internal.cuh"]
@@ -352,8 +357,14 @@ def run_ours(args):
         k64 = max(20, args.steps // 10)
         t64 = time_device(d64, k64, 3, stream, torch, None, 1)
         m64 = N * k64 / t64 / 1e6
+        fl = FP64_FLOP_PER_NODE * m64 * 1e6 / 1e9
         extras["fp64"] = {"value": round(m64, 1), "unit": "MLUPS", "tile": list(d64.tile()),
                           "hbm_frac_of_measured": round(BYTES_PER_NODE["fp64"] * N / (t64 / k64) / 1e9 / peak, 4),
+                          "roofline": {"bound": "alu", "achieved": round(fl, 1),
+                                       "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                                       "frac": round(fl / FP64_NOMINAL_GFLOPS, 4),
+                                       "peak_kind": "nominal FP64 (no measured FP64 peak)",
+                                       "flop_per_node": FP64_FLOP_PER_NODE},
                           "steps": k64}
         d64.close()
         dg = lbm.Domain(case.nx, case.ny, case.params, case.bc, prec="fp32_g16",
