@@ -75,6 +75,21 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(t, dist, world, device):
+    """The slowest rank's time: the whole job is done when every rank is."""
+    if world <= 1:
+        return t
+    import torch
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_mlups(world, nodes_per_rank, steps, t):
+    """Whole-job node updates per second (each rank steps its own domain)."""
+    return world * nodes_per_rank * steps / t / 1e6
+
+
 def step_source_hash():
     h = hashlib.sha256()
     for p in STEP_SOURCES:
@@ -299,11 +314,8 @@ def run_ours(args):
     dom.init_fields(*case.fields())
     with ClockSampler(local) as clk:
         t = time_device(dom, args.steps, args.warmup, stream, torch, dist, world)
-    if world > 1:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    mlups = world * N * args.steps / t / 1e6
+    t = max_over_ranks(t, dist, world, "cuda")
+    mlups = job_mlups(world, N, args.steps, t)
     ms_per_step = t / args.steps * 1e3
 
     # end to end through the C ABI with pinned host buffers: upload the
@@ -321,11 +333,8 @@ def run_ours(args):
     dom.get_rho_u_T(tuple(outs))
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e = {"value": round(world * N * e2e_steps / te / 1e6, 1), "unit": "MLUPS",
+    te = max_over_ranks(te, dist, world, "cuda")
+    e2e = {"value": round(job_mlups(world, N, e2e_steps, te), 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int(4 * N * 8 / e2e_steps),
            "d2h_bytes_per_step": int(4 * N * 8 / e2e_steps),
            "call": "lbm_init_fields(host) + lbm_step(%d) + lbm_get_rho_u_T(host)" % e2e_steps}
