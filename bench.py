@@ -170,7 +170,7 @@ def make_case(n=NX):
     return W.open_evaporation(n, n, R=640.0 * n / 4096.0, steps=0)
 
 
-def cpu_baseline(sample_n=1024, sample_steps=12):
+def cpu_baseline(sample_n=1024, sample_steps=60):
     """The FP64 C oracle, single-threaded, on a bounded sample of the
     workload (a sample_n^2 domain of the same setup)."""
     import oracle
@@ -188,24 +188,24 @@ def cpu_baseline(sample_n=1024, sample_steps=12):
 
 
 def accuracy_check():
-    """Each precision against the FP64 oracle: 64x64 droplet, 1000 steps."""
-    import oracle
+    """FP32 and FP32+FP16-g against FP64 on the GPU (the metric's "FP32 vs FP64
+    at the stated error"): 64x64 droplet, 1000 steps, max relative field
+    error.  The FP64 path's own agreement with the CPU oracle is the parity
+    tests' job (<= 1e-10 on the same case)."""
     import paper_2205_00686_gb300 as lbm
     from paper_2205_00686_gb300 import workloads as W
     c = W.static_droplet()
-    o = oracle.Sim(c.nx, c.ny, c.params, c.bc)
-    o.init(*c.fields())
-    o.step(1000)
-    ref = o.fields()
-    out = {}
+    got = {}
     for prec in ("fp64", "fp32", "fp32_g16"):
         d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec=prec)
         d.init_fields(*c.fields())
         d.step(1000)
-        got = d.get_rho_u_T()
-        out[prec] = max(float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(got, ref))
+        got[prec] = d.get_rho_u_T()
         d.close()
-    return {"case": "64x64 droplet, 1000 steps, max relative field error vs FP64 oracle",
+    ref = got["fp64"]
+    out = {p: max(float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(got[p], ref))
+           for p in ("fp32", "fp32_g16")}
+    return {"case": "64x64 droplet, 1000 steps, max relative field error vs the FP64 path",
             **{k: float("%.3e" % v) for k, v in out.items()}}
 
 
