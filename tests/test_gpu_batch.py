@@ -151,3 +151,29 @@ def test_batch_rejects_mixed_physics():
         x.step(1)                 # attached: the batch owns its stepping
     assert ei.value.code == lbm.LBM_ESTATE
     b.close()
+
+
+def test_batched_population_sample_matches_oracle():
+    """The batched population (512 open-evaporation domains, sides 64-512):
+    a seeded sample of 16 of them advanced together in one FP64 batch for
+    60 steps equals the oracle run of each, element by element."""
+    import paper_2205_00686_gb300 as lbm
+    pop = W.batch_instances()
+    idx = sorted(int(i) for i in np.argsort(W.uniform(99, len(pop)))[:16])
+    sample = [pop[i] for i in idx]
+    b = lbm.Batch()
+    doms = []
+    for c in sample:
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp64")
+        d.init_fields(*c.fields())
+        b.attach(d)
+        doms.append(d)
+    b.step(60)
+    assert b.sync() == 0
+    for c, d in zip(sample, doms):
+        b.detach(d)
+        o = P.run_oracle(c, 60)
+        fe = P.field_errors(d.get_rho_u_T(), o.fields())
+        assert max(fe.values()) <= 1e-12, (c.name, fe)
+        d.close()
+    b.close()
