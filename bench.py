@@ -24,6 +24,7 @@ import hashlib
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -116,7 +117,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples (the JSON line carries their summary); BENCH_CLOCKS_CSV
+        # names a file to keep them in
+        self.path = os.environ.get("BENCH_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), "lbm_bench_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
