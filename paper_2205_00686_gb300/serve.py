@@ -33,6 +33,11 @@ from typing import Callable, Dict, List, Optional
 import numpy as np
 
 
+# request outcomes besides the library's own negative codes
+CANCELLED = -100      # withdrawn by the client before it finished
+ADMIT_FAILED = -101   # its domain could not be created (device memory, bad input)
+
+
 @dataclasses.dataclass
 class Request:
     rid: int
@@ -44,6 +49,7 @@ class Request:
     result: Optional[tuple] = None      # (rho, ux, uy, T) host arrays
     error: int = 0
     done_steps: int = 0
+    detail: str = ""
 
     @property
     def latency(self) -> Optional[float]:
@@ -78,7 +84,12 @@ class CudaBackend:
         d = self.lbm.Domain(case.nx, case.ny, case.params, case.bc, prec=self.prec,
                             stream=self.stream.cuda_stream, device_mem=buf.data_ptr(),
                             device_bytes=nbytes)
-        d.init_fields(*case.fields())
+        try:
+            d.init_fields(*case.fields())
+        except Exception:
+            d.close()
+            del buf
+            raise
         key = self._key(case)
         if key not in self.batches:
             self.batches[key] = self.lbm.Batch(stream=self.stream.cuda_stream)
@@ -160,11 +171,34 @@ class Server:
             if self.mem_used + need > self.mem_budget:
                 break
             self.waiting.popleft()
-            h = self.backend.open(r.case)
+            try:
+                h = self.backend.open(r.case)
+            except Exception as e:      # allocation or creation failed: this request only
+                r.admitted = r.finished = self.clock()
+                r.error = ADMIT_FAILED
+                r.detail = str(e)
+                self.finished.append(r)
+                continue
             r.admitted = self.clock()
             self.active[r.rid] = (r, h, need)
             self.mem_used += need
             self.max_active = max(self.max_active, len(self.active))
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraws a request: a waiting one leaves the queue, an active one is
+        retired between chunks without reading its fields.  Returns False if it
+        had already finished (or never existed)."""
+        for r in list(self.waiting):
+            if r.rid == rid:
+                self.waiting.remove(r)
+                r.finished = self.clock()
+                r.error = CANCELLED
+                self.finished.append(r)
+                return True
+        if rid in self.active:
+            self._retire(rid, error=CANCELLED)
+            return True
+        return False
 
     def _retire(self, rid, error=0):
         r, h, need = self.active.pop(rid)
@@ -225,7 +259,8 @@ class Server:
         wall = (self.clock() - self.t_start) if self.t_start is not None else 0.0
         return {
             "requests": len(self.finished),
-            "failed": sum(1 for r in self.finished if r.error),
+            "failed": sum(1 for r in self.finished if r.error and r.error != CANCELLED),
+            "cancelled": sum(1 for r in self.finished if r.error == CANCELLED),
             "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
             "node_updates": int(self.node_updates),

@@ -52,3 +52,34 @@ def test_served_results_equal_solo_results():
         for a, b in zip(r.result, ref):
             assert np.array_equal(a, b), c.name
     del lbm
+
+
+def test_bad_request_and_cancellation_leave_the_others_exact():
+    """A request whose initial density is outside the EOS range fails at
+    admission (the library reports psi^2 < 0), one running request is
+    cancelled between chunks, and every other request still equals its solo
+    run bit for bit."""
+    from paper_2205_00686_gb300.serve import ADMIT_FAILED, CANCELLED, CudaBackend, Server
+    be = CudaBackend("fp32")
+    base = [c for _, c, _ in requests()[:4]]
+    bad = W.open_evaporation(64, 64, R=16.0, seed=7, steps=40)
+    bad.rho = bad.rho.copy()
+    bad.rho[32, 32] = 9.7
+    srv = Server(be, mem_budget=4 * be.bytes_for(base[-1]), chunk=10)
+    rs = [srv.submit(c, 40) for c in base[:2]]
+    rb = srv.submit(bad, 40)
+    rs += [srv.submit(c, 40) for c in base[2:]]
+    srv.tick()
+    victim = rs[1]
+    assert victim.rid in srv.active and srv.cancel(victim.rid)
+    while srv.tick():
+        pass
+    assert rb.error == ADMIT_FAILED and "-4" in rb.detail
+    assert victim.error == CANCELLED and victim.result is None
+    for r, c in zip(rs, base):
+        if r is victim:
+            continue
+        assert r.error == 0
+        for a, b in zip(r.result, solo(c, 40)):
+            assert np.array_equal(a, b), c.name
+    assert srv.mem_used == 0

@@ -16,10 +16,11 @@ class FakeCase:
 
 
 class FakeBackend:
-    def __init__(self, fail_tags=()):
+    def __init__(self, fail_tags=(), fail_open_tags=()):
         self.open_handles = {}
         self.log = []
         self.fail_tags = set(fail_tags)
+        self.fail_open_tags = set(fail_open_tags)
         self.peak_bytes = 0
         self._live_bytes = 0
 
@@ -27,6 +28,8 @@ class FakeBackend:
         return case.nx * case.ny * 100
 
     def open(self, case):
+        if case.tag in self.fail_open_tags:
+            raise MemoryError("device allocation failed")
         h = {"case": case, "steps": 0}
         self.open_handles[id(h)] = h
         self._live_bytes += self.bytes_for(case)
@@ -135,3 +138,44 @@ def test_timed_arrivals_are_admitted_while_others_run():
     assert st["requests"] == 2
     steps = [e for e in be.log if e[0] == "step"]
     assert any(e[2] == ["first", "later"] for e in steps)
+
+
+def test_failed_admission_fails_only_that_request():
+    """A domain whose creation fails (e.g. device memory exhausted) retires
+    its own request with ADMIT_FAILED; the budget is not charged and every
+    other request runs to completion."""
+    from paper_2205_00686_gb300.serve import ADMIT_FAILED
+    be = FakeBackend(fail_open_tags={"b"})
+    srv = Server(be, mem_budget=2 * 64 * 64 * 100, chunk=10, clock=Clock())
+    reqs = {t: srv.submit(FakeCase(64, 64, t), steps=30) for t in "abcd"}
+    while srv.tick():
+        pass
+    assert reqs["b"].error == ADMIT_FAILED and "allocation" in reqs["b"].detail
+    assert reqs["b"].result is None
+    for t in "acd":
+        assert reqs[t].error == 0 and reqs[t].result == 30
+    assert srv.mem_used == 0 and be.peak_bytes <= srv.mem_budget
+    st = srv.stats()
+    assert st["failed"] == 1 and st["requests"] == 4
+
+
+def test_cancel_waiting_and_running_requests():
+    """Cancelling a running request retires it between chunks without a
+    read-back and frees its memory for the queue; cancelling a queued one
+    removes it; a finished request cannot be cancelled."""
+    from paper_2205_00686_gb300.serve import CANCELLED
+    be = FakeBackend()
+    srv = Server(be, mem_budget=2 * 64 * 64 * 100, chunk=10, clock=Clock())
+    a, b, c, d = (srv.submit(FakeCase(64, 64, t), steps=50) for t in "abcd")
+    srv.tick()                      # a, b admitted; c, d waiting
+    assert set(srv.active) == {a.rid, b.rid}
+    assert srv.cancel(b.rid) and b.error == CANCELLED and b.result is None
+    assert ("close", "b") in be.log
+    assert srv.cancel(d.rid) and d.error == CANCELLED
+    while srv.tick():
+        pass
+    assert a.result == 50 and c.result == 50
+    assert not srv.cancel(a.rid) and not srv.cancel(12345)
+    assert ("open", "d") not in be.log
+    st = srv.stats()
+    assert st["cancelled"] == 2 and st["failed"] == 0 and st["requests"] == 4
