@@ -17,6 +17,8 @@ below follow them:
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 PERIODIC, WALL, OPEN = 0, 1, 2
@@ -354,3 +356,26 @@ def droplet_cloud3d(n=256, cells=4, R=None, w=4.0, Tr=0.86, amp=1e-4, seed=11, s
     T = np.full(rho.shape, Tr * TC)
     return Case3("droplet_cloud3d_%d_%dx%dx%d" % (n, cells, cells, cells), n, n, n,
                  p or params(), periodic_bc3(), rho, T, steps, rl, rg)
+
+
+# ---- named configurations (configs/*.json) -----------------------------------
+
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "configs")
+
+
+def load_config(name_or_path: str) -> dict:
+    """A named configuration: {"name", "about", "case", "args", "precisions",
+    "steps", ...}.  `name_or_path` is a file or a name under configs/."""
+    import json
+    path = name_or_path if os.path.exists(name_or_path) else os.path.join(
+        CONFIG_DIR, name_or_path + ".json")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def config_case(cfg: dict, **override):
+    """Builds the configuration's input (a Case, Case3, or a list of Cases)."""
+    fn = globals()[cfg["case"]]
+    args = dict(cfg.get("args", {}))
+    args.update(override)
+    return fn(**args)
