@@ -55,11 +55,13 @@ def test_served_results_equal_solo_results():
 
 
 def test_bad_request_and_cancellation_leave_the_others_exact():
-    """A request whose initial density is outside the EOS range fails at
-    admission (the library reports psi^2 < 0), one running request is
-    cancelled between chunks, and every other request still equals its solo
-    run bit for bit."""
-    from paper_2205_00686_gb300.serve import ADMIT_FAILED, CANCELLED, CudaBackend, Server
+    """A request whose initial density is outside the EOS range fails alone
+    at its first chunk (the step kernel reports psi^2 < 0 in the domain's
+    sticky error word; lbm_init_fields does not evaluate the EOS), one running
+    request is cancelled between chunks, and every other request still equals
+    its solo run bit for bit."""
+    import paper_2205_00686_gb300 as lbm
+    from paper_2205_00686_gb300.serve import CANCELLED, CudaBackend, Server
     be = CudaBackend("fp32")
     base = [c for _, c, _ in requests()[:4]]
     bad = W.open_evaporation(64, 64, R=16.0, seed=7, steps=40)
@@ -74,7 +76,7 @@ def test_bad_request_and_cancellation_leave_the_others_exact():
     assert victim.rid in srv.active and srv.cancel(victim.rid)
     while srv.tick():
         pass
-    assert rb.error == ADMIT_FAILED and "-4" in rb.detail
+    assert rb.error == lbm.LBM_EPSI and rb.result is None and rb.done_steps == 10
     assert victim.error == CANCELLED and victim.result is None
     for r, c in zip(rs, base):
         if r is victim:
