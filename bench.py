@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--tile", default=None,
                     help="THREADS,ROWS: fixed tile instead of the autotuner (profiler captures)")
+    ap.add_argument("--staging", default="auto", choices=["auto", "on", "off"],
+                    help="load path of the FP32 step: bulk-copy staging on/off (auto: the "
+                         "autotuner's choice, else on where possible)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-instances", type=int, default=512)
     ap.add_argument("--serve-steps", type=int, default=500)
@@ -314,7 +317,9 @@ def run_ours(args):
     if args.tile:
         dom.set_tile(*[int(v) for v in args.tile.split(",")])
     elif not args.no_tune:
-        dom.autotune(10)          # tile chosen by timed trials on a scratch domain
+        dom.autotune(10)          # tile and load path chosen by timed trials on a scratch domain
+    if args.staging != "auto":
+        dom.staged = args.staging == "on"
     dom.init_fields(*case.fields())
     with ClockSampler(local) as clk:
         t = time_device(dom, args.steps, args.warmup, stream, torch, dist, world)
@@ -357,8 +362,10 @@ def run_ours(args):
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": "%s hbm_gbs (copy)" % peak_kind,
                 "algorithmic_bytes_per_node": BYTES_PER_NODE[args.prec],
-                "kernel": "lbm::k_step<%d,%d>" % ({"fp64": 0, "fp32": 1, "fp32_g16": 2}[args.prec],
-                                                  dom.tile()[0])}
+                "kernel": "lbm::k_step<%d,%d>%s" % ({"fp64": 0, "fp32": 1, "fp32_g16": 2}[args.prec],
+                                                    dom.tile()[0],
+                                                    " (rows staged by bulk copies)" if dom.staged
+                                                    else " (register-prefetched rows)")}
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -412,7 +419,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (%.2f GiB state)"
                          % (BYTES_PER_NODE[args.prec] * N / 2 ** 30),
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "tile": list(dom.tile())},
+                   "tile": list(dom.tile()), "staged": dom.staged},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
         "gpu_launches": args.steps,
         **extras,

@@ -40,6 +40,7 @@ extern "C" {
 #define LBM_EIO (-6)         /* checkpoint file could not be read or written  */
 #define LBM_ESTATE (-7)      /* call out of order (e.g. step before init)     */
 #define LBM_ETOOBIG (-8)     /* size beyond a fixed capacity (no-alloc entry)  */
+#define LBM_ETIMEOUT (-9)    /* a bounded device wait ran out (staged rows)    */
 
 /* ---- precision of storage and arithmetic ------------------------------- */
 typedef enum {
@@ -280,12 +281,28 @@ void lbm_batch_destroy(lbm_batch* b);
 
 /* ---- launch configuration ------------------------------------------------ *
  * Tile of the fused step: a strip of (threads - 8) columns swept over a
- * segment of `rows` rows.  threads is 128 or 256; rows >= 1.  The autotuner
+ * segment of `rows` rows.  threads is 128, 224 or 256; rows >= 1.  The autotuner
  * times the candidates on a scratch domain of the same size and precision
  * and applies the fastest; its choice is cached per (precision, size). */
 int lbm_set_tile(lbm_ctx* ctx, int threads, int rows);
 int lbm_get_tile(const lbm_ctx* ctx, int* threads, int* rows);
 int lbm_autotune(lbm_ctx* ctx, int steps_per_trial);
+
+/* Load path of the fused FP32 step (no counterpart in the paper, which
+ * prescribes no implementation).  on = 1: each row of f, g and P^{n-1} that a
+ * tile needs is brought into shared memory by bulk asynchronous copies
+ * (cp.async.bulk, completion tracked by an mbarrier) a full row ahead of its
+ * use; on = 0: each thread loads its own column a half row ahead into
+ * registers.  The two paths compute identical results (same arithmetic in
+ * the same order).  Staging needs FP32 storage and either open x edges or a
+ * periodic x axis with nx a multiple of 4 (nx >= 32); lbm_create turns it on
+ * where it is possible, lbm_autotune times both paths.  Returns LBM_EINVAL
+ * when on = 1 is not possible, LBM_ESTATE for a context in a batch.  A
+ * staged launch that waits more than about a second for a row reports
+ * LBM_ETIMEOUT (sticky) instead of hanging.  lbm_get_staging returns 0 or 1
+ * (LBM_EINVAL for NULL).  A batch stages when every member can. */
+int lbm_set_staging(lbm_ctx* ctx, int on);
+int lbm_get_staging(const lbm_ctx* ctx);
 
 /* ---- diagnostics without any allocation -------------------------------- *
  * The paper has no counterpart to this call; it exists for callers that may

@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ENONFINITE, LBM_EPSI, LBM_ECUDA, LBM_EIO, LBM_ESTATE = (
     0, -1, -2, -3, -4, -5, -6, -7)
 LBM_ETOOBIG = -8
+LBM_ETIMEOUT = -9
 LBM_NOALLOC_MAX_NODES = 33554432
 LBM_FP64, LBM_FP32, LBM_FP32_G16 = 0, 1, 2
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp32_g16": LBM_FP32_G16}
@@ -37,7 +38,7 @@ ABI_FUNCTIONS = (
     "lbm_step_count", "lbm_sync", "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
     "lbm_batch_create", "lbm_batch_attach", "lbm_batch_detach", "lbm_batch_size",
     "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy", "lbm_set_tile", "lbm_get_tile",
-    "lbm_autotune", "lbm_diag_reduce_noalloc", "lbm_reconfigure", "lbm_contact_angle",
+    "lbm_autotune", "lbm_set_staging", "lbm_get_staging", "lbm_diag_reduce_noalloc", "lbm_reconfigure", "lbm_contact_angle",
     "lbm_regions",
     # include/lbm3d.h
     "lbm3d_state_bytes", "lbm3d_create", "lbm3d_init_fields", "lbm3d_step", "lbm3d_get_fields",
@@ -135,6 +136,8 @@ def lib():
             "lbm_get_tile": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                              ctypes.c_int),
             "lbm_autotune": ([_vp, ctypes.c_int], ctypes.c_int),
+            "lbm_set_staging": ([_vp, ctypes.c_int], ctypes.c_int),
+            "lbm_get_staging": ([_vp], ctypes.c_int),
             "lbm_diag_reduce_noalloc": ([_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, _vp, _vp],
                                         ctypes.c_int),
@@ -304,6 +307,16 @@ class Domain:
     def autotune(self, steps_per_trial: int = 10):
         _check(lib().lbm_autotune(self._h, steps_per_trial), self._h)
         return self.tile()
+
+    @property
+    def staged(self) -> bool:
+        """True when the FP32 step brings its rows in by bulk asynchronous
+        copies (see lbm_set_staging)."""
+        return lib().lbm_get_staging(self._h) == 1
+
+    @staged.setter
+    def staged(self, on: bool):
+        _check(lib().lbm_set_staging(self._h, 1 if on else 0), self._h)
 
     @property
     def last_error(self) -> str:

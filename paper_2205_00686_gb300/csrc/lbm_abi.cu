@@ -107,9 +107,12 @@ uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
     return ~crc;
 }
 
-// tile autotuner cache: (prec, nx, ny) -> (threads, rows)
-std::map<std::tuple<int, int, int>, std::pair<int, int>>& tune_cache() {
-    static std::map<std::tuple<int, int, int>, std::pair<int, int>> m;
+// tile autotuner cache: (prec, nx, ny) -> (threads, rows, staged)
+struct Tile {
+    int threads, rows, staged;
+};
+std::map<std::tuple<int, int, int>, Tile>& tune_cache() {
+    static std::map<std::tuple<int, int, int>, Tile> m;
     return m;
 }
 
@@ -142,16 +145,38 @@ bool has_walls(const Inst& I) {
     return I.flow[2] == LBM_WALL || I.flow[3] == LBM_WALL;
 }
 
-// default segment height: 64 rows (7 pipeline-fill rows per segment stay
-// ~10% of the sweep) unless that leaves the persistent grid without at least
-// one unit per resident CTA; never below 8
-int default_rows(int prec, int threads, int walls, int nx, int ny) {
+// default load path and tile: bulk-copy staging on a 224-thread tile (two
+// CTAs per SM, two rows in flight per CTA) where the domains can take it,
+// have no walls (the wall rings would leave one CTA per SM) and are wide
+// enough that 216-column strips waste no more than 10 % more thread columns
+// than 120-column ones (the staged step is ~10 % faster per thread column on
+// 4096^2; a 64-wide domain fills 29 % of a 224-thread strip, 50 % of a
+// 128-thread one); otherwise the register-prefetch form on 128 threads
+// (four CTAs per SM)
+long long strip_columns(int nx, int threads) {
+    return (long long)((nx + threads - 9) / (threads - 8)) * threads;
+}
+bool default_staged(const Inst* const* I, size_t n, int prec) {
+    long long c224 = 0, c128 = 0;
+    for (size_t i = 0; i < n; ++i) {
+        if (!stage_eligible(*I[i], prec) || has_walls(*I[i])) return false;
+        c224 += strip_columns(I[i]->nx, 224) * I[i]->ny;
+        c128 += strip_columns(I[i]->nx, 128) * I[i]->ny;
+    }
+    return n > 0 && 10 * c224 <= 11 * c128;
+}
+int default_threads(int staged) { return staged ? 224 : 128; }
+
+// default segment height: the tallest of 256, 128, 64, ... rows (each
+// segment re-sweeps 6 halo rows) that still gives the persistent grid at
+// least one unit per resident CTA; never below 8
+int default_rows(int prec, int threads, int walls, int staged, int nx, int ny) {
     int ctas = 1;
     size_t smem = 0;
-    step_occupancy(prec, threads, walls, &ctas, &smem);
+    step_occupancy(prec, threads, walls, staged, &ctas, &smem);
     const long long slots = (long long)std::max(ctas, 1) * num_sms();
     const int strips = (nx + threads - 9) / (threads - 8);
-    int rows = 64;
+    int rows = 256;
     while (rows > 8 && (long long)strips * ((ny + rows - 1) / rows) < slots) rows /= 2;
     return std::max(1, std::min(rows, ny));
 }
@@ -175,7 +200,7 @@ struct lbm_ctx {
     Inst* inst_dev = nullptr;
     unsigned* sched = nullptr;
     Unit* units = nullptr;
-    int n_units = 0, grid = 1, threads = 128, rows = 64;
+    int n_units = 0, grid = 1, threads = 128, rows = 64, staged = 0;
     cudaGraphExec_t graph = nullptr;
     long long step = 0;
     bool initialized = false;
@@ -196,7 +221,7 @@ struct lbm_batch {
     Inst* insts = nullptr;
     Unit* units = nullptr;
     unsigned* sched = nullptr;
-    int n_units = 0, grid = 1, threads = 128, rows = 64, prec = -1, walls = 0;
+    int n_units = 0, grid = 1, threads = 128, rows = 64, prec = -1, walls = 0, staged = 0;
     PhysD phys;
     lbm_params params;
     cudaGraphExec_t graph = nullptr;
@@ -222,6 +247,7 @@ static int cuda_err(lbm_ctx* c, cudaError_t e, const char* where) {
 static int map_device_err(int bits) {
     if (bits & ERR_PSI) return LBM_EPSI;
     if (bits & ERR_NONFINITE) return LBM_ENONFINITE;
+    if (bits & ERR_TIMEOUT) return LBM_ETIMEOUT;
     return LBM_OK;
 }
 
@@ -230,13 +256,15 @@ static void drop_graph(cudaGraphExec_t* g) {
     *g = nullptr;
 }
 
-// (re)builds the unit list and persistent grid of a context for its tile
-static int ctx_apply_tile(lbm_ctx* c, int threads, int rows) {
+// (re)builds the unit list and persistent grid of a context for its tile and
+// load path (staged: bulk-copy staging of the FP32 rows where eligible)
+static int ctx_apply_tile(lbm_ctx* c, int threads, int rows, int staged) {
+    staged = staged && stage_eligible(c->inst, c->prec) ? 1 : 0;
     std::vector<Unit> us;
     build_units(c->inst, 0, threads, rows, us);
     int ctas = 1;
     size_t smem = 0;
-    if (step_occupancy(c->prec, threads, has_walls(c->inst), &ctas, &smem))
+    if (step_occupancy(c->prec, threads, has_walls(c->inst), staged, &ctas, &smem))
         return set_err(c, LBM_ECUDA, "occupancy query failed");
     if (ctas < 1) return set_err(c, LBM_EINVAL, "tile does not fit on an SM");
     cudaStreamSynchronize(c->stream);
@@ -250,6 +278,7 @@ static int ctx_apply_tile(lbm_ctx* c, int threads, int rows) {
     c->grid = (int)std::min<long long>((long long)c->n_units, (long long)ctas * num_sms());
     c->threads = threads;
     c->rows = rows;
+    c->staged = staged;
     drop_graph(&c->graph);
     return LBM_OK;
 }
@@ -263,6 +292,7 @@ static StepLaunch ctx_launch(const lbm_ctx* c) {
     L.sched = c->sched;
     L.grid = c->grid;
     L.walls = has_walls(c->inst) ? 1 : 0;
+    L.staged = c->staged;
     L.phys = c->phys;
     return L;
 }
@@ -431,15 +461,17 @@ int lbm_create(int nx, int ny, const lbm_params* params, const lbm_bc* bc, int p
         return rc;
     }
     auto it = tune_cache().find(std::make_tuple(prec, nx, ny));
-    int threads = 128, rows = 0;
+    const Inst* Ip = &I;
+    int staged = default_staged(&Ip, 1, prec) ? 1 : 0, threads = default_threads(staged), rows = 0;
     if (it != tune_cache().end()) {
-        threads = it->second.first;
-        rows = it->second.second;
+        threads = it->second.threads;
+        rows = it->second.rows;
+        staged = it->second.staged;
     } else {
         rows = default_rows(prec, threads, (bc->flow[2] == LBM_WALL || bc->flow[3] == LBM_WALL) ? 1 : 0,
-                            nx, ny);
+                            staged, nx, ny);
     }
-    int rc = ctx_apply_tile(c, threads, rows);
+    int rc = ctx_apply_tile(c, threads, rows, staged);
     if (rc) {
         lbm_destroy(c);
         return rc;
@@ -918,10 +950,20 @@ int lbm_regions(lbm_ctx* c, double threshold, int below, int* labels, lbm_region
 
 // ---- tile / autotune ------------------------------------------------------
 int lbm_set_tile(lbm_ctx* c, int threads, int rows) {
-    if (!c || (threads != 128 && threads != 256) || rows < 1) return LBM_EINVAL;
+    if (!c || (threads != 128 && threads != 224 && threads != 256) || rows < 1) return LBM_EINVAL;
     if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
-    return ctx_apply_tile(c, threads, std::min(rows, c->ny));
+    return ctx_apply_tile(c, threads, std::min(rows, c->ny), c->staged);
 }
+
+int lbm_set_staging(lbm_ctx* c, int on) {
+    if (!c) return LBM_EINVAL;
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    if (on && !stage_eligible(c->inst, c->prec))
+        return set_err(c, LBM_EINVAL, "bulk-copy staging needs FP32 and open x or nx % 4 == 0");
+    return ctx_apply_tile(c, c->threads, c->rows, on ? 1 : 0);
+}
+
+int lbm_get_staging(const lbm_ctx* c) { return c ? c->staged : LBM_EINVAL; }
 
 int lbm_get_tile(const lbm_ctx* c, int* threads, int* rows) {
     if (!c) return LBM_EINVAL;
@@ -950,32 +992,36 @@ int lbm_autotune(lbm_ctx* c, int steps) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bt = c->threads, br = c->rows;
-    const int thr_c[2] = {128, 256};
+    int bt = c->threads, br = c->rows, bs = c->staged;
+    const int thr_c[3] = {128, 224, 256};
     const int rows_c[6] = {16, 32, 64, 128, 256, 512};
-    for (int ti = 0; ti < 2; ++ti)
-        for (int ri = 0; ri < 6; ++ri) {
-            int rows = std::min(rows_c[ri], c->ny);
-            if (ri > 0 && rows_c[ri - 1] >= c->ny) continue;
-            if (ctx_apply_tile(s, thr_c[ti], rows)) continue;
-            lbm_step(s, 2);
-            cudaEventRecord(e0, s->stream);
-            lbm_step(s, steps);
-            cudaEventRecord(e1, s->stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) continue;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                bt = thr_c[ti];
-                br = rows;
+    const int n_paths = stage_eligible(c->inst, c->prec) ? 2 : 1;
+    for (int si = 0; si < n_paths; ++si)
+        for (int ti = 0; ti < 3; ++ti)
+            for (int ri = 0; ri < 6; ++ri) {
+                int rows = std::min(rows_c[ri], c->ny);
+                if (ri > 0 && rows_c[ri - 1] >= c->ny) continue;
+                const int staged = n_paths == 2 ? 1 - si : 0;
+                if (ctx_apply_tile(s, thr_c[ti], rows, staged)) continue;
+                lbm_step(s, 2);
+                cudaEventRecord(e0, s->stream);
+                lbm_step(s, steps);
+                cudaEventRecord(e1, s->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    bt = thr_c[ti];
+                    br = rows;
+                    bs = staged;
+                }
             }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     lbm_destroy(s);
-    tune_cache()[std::make_tuple(c->prec, c->nx, c->ny)] = std::make_pair(bt, br);
-    return ctx_apply_tile(c, bt, br);
+    tune_cache()[std::make_tuple(c->prec, c->nx, c->ny)] = Tile{bt, br, bs};
+    return ctx_apply_tile(c, bt, br, bs);
 }
 
 // ---- batch ---------------------------------------------------------------
@@ -990,9 +1036,16 @@ static int batch_rebuild(lbm_batch* b) {
     std::vector<Inst> hi;
     std::vector<Unit> us;
     b->walls = 0;
+    std::vector<const Inst*> ip;
     for (size_t i = 0; i < b->members.size(); ++i) {
         hi.push_back(b->members[i]->inst);
+        ip.push_back(&b->members[i]->inst);
         if (has_walls(b->members[i]->inst)) b->walls = 1;
+    }
+    // bulk-copy staging (224-thread tile) when the members as a whole take it
+    b->staged = default_staged(ip.data(), ip.size(), b->prec) ? 1 : 0;
+    b->threads = default_threads(b->staged);
+    for (size_t i = 0; i < b->members.size(); ++i) {
         build_units(b->members[i]->inst, (int)i, b->threads, std::min(b->rows, b->members[i]->ny), us);
     }
     // longest-first is not needed: units of one batch are near-equal in size;
@@ -1005,7 +1058,7 @@ static int batch_rebuild(lbm_batch* b) {
     b->n_units = (int)us.size();
     int ctas = 1;
     size_t smem = 0;
-    step_occupancy(b->prec, b->threads, b->walls, &ctas, &smem);
+    step_occupancy(b->prec, b->threads, b->walls, b->staged, &ctas, &smem);
     b->grid = (int)std::min<long long>((long long)b->n_units, (long long)std::max(ctas, 1) * num_sms());
     return LBM_OK;
 }
@@ -1081,6 +1134,7 @@ int lbm_batch_step(lbm_batch* b, int n) {
     L.sched = b->sched;
     L.grid = b->grid;
     L.walls = b->walls;
+    L.staged = b->staged;
     L.phys = b->phys;
     int rc = enqueue_steps(b->stream, &b->graph, L, b->prec, b->threads, n, b->members[0]);
     if (rc == LBM_OK)

@@ -15,8 +15,8 @@ enum { PERIODIC = 0, WALL = 1, OPEN = 2 };
 enum { T_PERIODIC = 0, T_DIRICHLET = 1, T_ADIABATIC = 2 };
 enum { EW = 0, EE = 1, ES = 2, EN = 3 };
 
-// sticky device error bits
-enum { ERR_PSI = 1, ERR_NONFINITE = 2 };
+// sticky device error bits (ERR_TIMEOUT: a bounded wait for a staged row ran out)
+enum { ERR_PSI = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
 
 // Device-resident control block of one domain: the device-side step counter
 // read by every launch, the three-slot ring of per-step density sums used by
@@ -213,11 +213,24 @@ struct StepLaunch {
     unsigned* sched;   // [0] next unit, [1] finished CTAs
     int grid;
     int walls;         // some domain has a wall: the launch carries the wall rings
+    int staged;        // FP32 only: rows arrive by bulk copies (stage_eligible)
     PhysD phys;
 };
 
+// The bulk-copy staged form of the FP32 step needs every copied row segment
+// to start on a 16-byte boundary: always true for open x edges (the copy of
+// the last strip is rounded up into the row's pitch padding), and for
+// periodic x when nx is a multiple of 4 (the wrapped pieces then start on
+// 4-column boundaries) and the window wraps at most a few times (nx >= 32).
+inline bool stage_eligible(const Inst& I, int prec) {
+    if (prec != 1) return false;
+    if (I.flow[EW] != PERIODIC) return true;
+    return I.nx % 4 == 0 && I.nx >= 32;
+}
+
 int step_launch(int prec, int threads, const StepLaunch& L, cudaStream_t st);
-int step_occupancy(int prec, int threads, int walls, int* ctas_per_sm, size_t* smem_bytes);
+int step_occupancy(int prec, int threads, int walls, int staged, int* ctas_per_sm,
+                   size_t* smem_bytes);
 
 int init_launch(int prec, const Inst* I_dev, const Inst& I, const double* rho, const double* ux,
                 const double* uy, const double* T, double w_dot, cudaStream_t st);

@@ -25,12 +25,24 @@
 // segment, served mostly by L2) and written once.  There are no tensor-core
 // contractions here: the step is a bandwidth-bound stencil.
 //
+// Two load paths feed stage A.  In the register-prefetch form each thread
+// loads its column of row k + 1 into registers during phase beta of
+// iteration k.  In the staged form (FP32) the rows arrive in shared memory by
+// bulk asynchronous copies (cp.async.bulk, one mbarrier per row in flight),
+// issued two iterations ahead of their use, and g and P^{n-1} stay in their
+// staging slots until stages C and D5 have used them.  A bandwidth-bound
+// sweep moves (bytes in flight per SM) / (loaded HBM latency); one row per
+// thread in registers caps that at about 30 KB per SM, two staged rows per
+// CTA of the 224-thread tile (two CTAs per SM) double it.
+//
 // The CTAs are persistent and pull (domain, strip, segment) units from an
 // atomic counter, so one launch serves one domain or hundreds of domains of
 // uneven size; the last CTA to finish advances every domain's device-side
 // step counter, clears the next slot of its density-sum ring and resets the
 // counter, which makes the launch replayable inside a CUDA graph.  No CTA
 // ever waits on another.
+#include <type_traits>
+
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -69,6 +81,87 @@ struct WallRings {
     R T[3][NT];
 };
 
+// Shared-memory layout of the bulk-copy staged form (FP32).  The rows of f,
+// g and P^{n-1} arrive by cp.async.bulk (the copy engine of each SM, tracked
+// by one mbarrier per in-flight row) instead of per-thread loads, two rows
+// ahead of their use.  The step moves its bytes at the rate
+// (bytes in flight per SM) / (loaded HBM latency); the register-prefetch form
+// holds one row in flight, this form two, without spending registers.  f is
+// needed only by stage A of its own row (three slots: the row being used, two
+// rows in flight); g and P^{n-1} stay in their slots until stages C and D5 of
+// the row, four iterations later (seven slots), which replaces the
+// per-column ring of the register-prefetch form.  After stage C reads
+// P^{n-1} of a row, that plane holds the row's g*_4.
+template <class R, int NT>
+struct StageSmem {
+    R fR[3][9][NT];
+    R gR[7][6][NT];
+    R psi[3][NT];
+    typename Vec2<R>::T u[3][NT];
+    R fs[3][9][NT];
+    R gs[3][3][NT];
+    typename Vec2<R>::T own[5][NT];   // rho, then T (dp/dT)_rho -> g*_0 after stage C
+    unsigned long long mbar[3];
+    double red[NT / 32];
+    int unit;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* m, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* m, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)),
+                 "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy completing on mbarrier m; dst, src 16-byte
+// aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(m))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* m, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// generic-proxy shared-memory writes of this thread ordered before later
+// bulk copies into the same bytes
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// bounded wait for a staged row: gives up after ~2^31 clocks (about a
+// second) and reports it; a thread that gave up stops waiting for the rest of
+// the launch (its results are then invalid and the sticky error says so)
+__device__ __forceinline__ void wait_row(unsigned long long* m, unsigned parity, int* err) {
+    if (*err & ERR_TIMEOUT) return;
+    if (mbar_test(m, parity)) return;
+    const long long t0 = clock64();
+    while (!mbar_test(m, parity)) {
+        if (clock64() - t0 > (1LL << 31)) {
+            *err |= ERR_TIMEOUT;
+            return;
+        }
+    }
+}
+
 // ghost-layer psi of a wall (Section 3.3): rho_ghost = rho(layer 2) +
 // tan(pi/2 - theta) |rho(x+1, layer 1) - rho(x-1, layer 1)|
 template <class R>
@@ -86,17 +179,19 @@ __device__ __forceinline__ R ghost_psi(const Phys<R>& P, R rho_far, R rho_p, R r
 // all active on interior rows, so it carries no row conditions and no
 // boundary branches and each phase compiles to one block of independent
 // work (the stages only touch different rows and ring slots).
-template <int PREC, int NT, bool UNIT>
+template <int PREC, int NT, bool UNIT, bool STG>
 struct Sweep {
     typedef typename Types<PREC>::R R;
     typedef typename Types<PREC>::TF TF;
     typedef typename Types<PREC>::TG TG;
     typedef typename Vec2<R>::T R2;
     typedef typename Vec4<R>::T R4;
+    typedef typename std::conditional<STG, StageSmem<R, NT>, StepSmem<R, NT>>::type SM;
+    static_assert(!STG || PREC == 1, "the staged form is FP32 only");
 
     const Inst& I;
     const Phys<R>& P;
-    StepSmem<R, NT>& S;
+    SM& S;
     WallRings<R, NT>& WR;   // valid only for domains with walls
     int t, nx, ny, pitch, y0, y1;
     bool perx, pery, first, use_mass, wallS, wallN;
@@ -119,9 +214,16 @@ struct Sweep {
     R mass_acc;
     int errbits;
     int ra0, ra1, ra2, b0, kw;
+    // staged form: window start column, this column's index in a staged row,
+    // slot of row k in the g/P ring (of 7), slot and mbarrier of row k in the
+    // f ring (of 3), and the phase parity each f mbarrier completes next
+    // (bit m for mbarrier m; the f ring and the mbarriers carry over from
+    // one unit to the next)
+    int X0w, sidx, gq, fq, kw2, scs;
+    unsigned mph, sbytes, rbytes;
 
-    __device__ __forceinline__ Sweep(const Inst& I_, const Unit& U, const Phys<R>& P_,
-                                     StepSmem<R, NT>& S_, WallRings<R, NT>& WR_)
+    __device__ __forceinline__ Sweep(const Inst& I_, const Unit& U, const Phys<R>& P_, SM& S_,
+                                     WallRings<R, NT>& WR_, int fq0, unsigned mph0)
         : I(I_), P(P_), S(S_), WR(WR_) {
         t = threadIdx.x;
         nx = I.nx;
@@ -219,7 +321,71 @@ struct Sweep {
         // wrapped row of k for loads
         kw = pery ? wrapi(y0 - 3, ny) : y0 - 3;
         // the populations of the first row A works on
-        load_row(y0 - 3, kw);
+        X0w = x0 - 4;
+        sidx = perx ? t : gxl - X0w;
+        gq = 0;
+        fq = fq0;
+        mph = mph0;
+        if constexpr (STG) {
+            // copy extent of one plane row: open x copies the columns inside
+            // the domain, periodic x the whole window
+            scs = perx ? X0w : max(X0w, 0);
+            const int sce = perx ? X0w + NT : ((min(X0w + NT, nx) + 3) & ~3);
+            sbytes = (unsigned)((sce - scs) * (int)sizeof(R));
+            rbytes = 15u * sbytes;
+            // wrapped rows y0 - 3 (kw), y0 - 2, y0 - 1; iteration k queues the
+            // copies of row k + 2 and arms row k + 3
+            const int kwa = (pery && kw == ny - 1) ? 0 : kw + 1;
+            kw2 = (pery && kwa == ny - 1) ? 0 : kwa + 1;
+            const int f1 = fq == 2 ? 0 : fq + 1, f2 = f1 == 2 ? 0 : f1 + 1;
+            arm_row(y0 - 3, fq);
+            arm_row(y0 - 2, f1);
+            arm_row(y0 - 1, f2);
+            __syncthreads();
+            issue_row(y0 - 3, kw, 0, fq);
+            issue_row(y0 - 2, kwa, 1, f1);
+        } else {
+            load_row(y0 - 3, kw);
+        }
+    }
+
+    // staged form.  Thread 0 arms the mbarrier of row k (f slot fslot) with
+    // the row's byte count one iteration before the row's copies go out, so
+    // that a barrier orders the arming before every copy; a row outside a
+    // non-periodic domain (or past the segment) arms with no bytes.
+    __device__ __forceinline__ void arm_row(int k, int fslot) {
+        if (t == 0) mbar_arrive_tx(&S.mbar[fslot], (k < y1 + 3 && rowvalid(k)) ? rbytes : 0u);
+    }
+    // The bulk copies of row k (wrapped row kwr) into f slot fslot and g/P
+    // slot gslot.  The 15 planes are spread over the warps (plane = warp +
+    // nwarps * lane: 0..8 f, 9..13 g, 14 P) so that no warp carries the issue
+    // work alone.  Open x: the columns inside the domain (the last strip's
+    // copy rounded up to 4 columns, inside the row pitch); clamped columns
+    // read their edge column's entry (sidx).  Periodic x: the window in pieces
+    // that wrap around the axis.
+    __device__ __forceinline__ void issue_row(int k, int kwr, int gslot, int fslot) {
+        if (!(k < y1 + 3 && rowvalid(k))) return;
+        constexpr int NW = NT / 32;
+        const int pl = (t >> 5) + NW * (t & 31);
+        if (pl >= 15) return;
+        unsigned long long* mb = &S.mbar[fslot];
+        const size_t rowoff = (size_t)kwr * pitch;
+        const R* src = pl < 9    ? (const R*)fsrc + (size_t)pl * plane + rowoff
+                       : pl < 14 ? (const R*)gsrc + (size_t)(pl - 9) * plane + rowoff
+                                 : Psrc + rowoff;
+        R* dst = pl < 9 ? &S.fR[fslot][pl][0] : &S.gR[gslot][pl < 14 ? pl - 9 : 5][0];
+        if (!perx) {
+            bulk_g2s(dst + (scs - X0w), src + scs, sbytes, mb);
+        } else {
+            int c = X0w;
+            const int end = X0w + NT;
+            while (c < end) {
+                const int wc = wrapi(c, nx);
+                const int n = min(end - c, nx - wc);
+                bulk_g2s(dst + (c - X0w), src + wc, (unsigned)(n * sizeof(R)), mb);
+                c += n;
+            }
+        }
     }
 
     __device__ __forceinline__ bool rowvalid(int r) const { return pery || (r >= 0 && r < ny); }
@@ -251,6 +417,17 @@ struct Sweep {
     __device__ __forceinline__ void iter(int k, const int a0, const int a1, const int a2) {
         const int bC = b0 >= 3 ? b0 - 3 : b0 + 2;   // slot5(k - 3)
         const int bD = b0 >= 4 ? b0 - 4 : b0 + 1;   // slot5(k - 4)
+        const int kwn = (pery && kw == ny - 1) ? 0 : kw + 1;
+        // staged form: g/P slots of rows k - 3 and k - 4; the copies of row
+        // k + 2 go out now, two iterations before stage A needs them (the f
+        // slot they fill held row k - 1, the g/P slot row k - 5: both were
+        // last read before the previous iteration's closing barrier)
+        const int gC = gq >= 3 ? gq - 3 : gq + 4;
+        const int gD = gq >= 4 ? gq - 4 : gq + 3;
+        if constexpr (STG) {
+            if (k + 2 <= y1 + 3)
+                issue_row(k + 2, kw2, gq >= 5 ? gq - 5 : gq + 2, fq == 0 ? 2 : fq - 1);
+        }
         // ================= phase alpha =================
         const bool doA = STEADY || (k < y1 + 3 && rowvalid(k));
 
@@ -258,10 +435,24 @@ struct Sweep {
         {
             const int r = k - 3;
             if (STEADY || (r >= y0 - 1 && r < y1 + 1 && rowvalid(r) && inC)) {
-                const R4 o0 = S.own[bC][0][t];
-                const R4 o1 = S.own[bC][1][t];
-                const R g0 = o0.x, g1 = o0.y, g2 = o0.z, g3 = o0.w, g4 = o1.x;
-                const R rho = o1.y, Pp = o1.z, TdpdT = o1.w;
+                R g0, g1, g2, g3, g4, rho, Pp, TdpdT;
+                if constexpr (STG) {
+                    const R* gr = &S.gR[gC][0][sidx];
+                    g0 = gr[0];
+                    g1 = gr[NT];
+                    g2 = gr[2 * NT];
+                    g3 = gr[3 * NT];
+                    g4 = gr[4 * NT];
+                    Pp = gr[5 * NT];
+                    const R2 ow = S.own[bC][t];
+                    rho = ow.x;
+                    TdpdT = ow.y;
+                } else {
+                    const R4 o0 = S.own[bC][0][t];
+                    const R4 o1 = S.own[bC][1][t];
+                    g0 = o0.x; g1 = o0.y; g2 = o0.z; g3 = o0.w; g4 = o1.x;
+                    rho = o1.y; Pp = o1.z; TdpdT = o1.w;
+                }
                 const R Td = ((g0 + g1) + (g2 + g3)) + g4;
                 const R m1 = g1 - g3;
                 const R m2 = g2 - g4;
@@ -327,12 +518,25 @@ struct Sweep {
                 S.gs[a0][0][t] = gs1;
                 S.gs[a0][1][t] = gs2;
                 S.gs[a0][2][t] = gs3;
-                R4 oo;
-                oo.x = g4;
-                oo.y = rho;
-                oo.z = gs0;
-                oo.w = gs4;
-                S.own[bC][1][t] = oo;
+                if constexpr (STG) {
+                    // g*_0 replaces T (dp/dT)_rho, g*_4 the consumed P^{n-1}.
+                    // g*_4 goes to position t, not sidx: at open x edges the
+                    // clamped halo columns (which run stage C in the steady
+                    // loop) share the edge column's sidx, while position t
+                    // is theirs alone (outside every valid column's sidx)
+                    R2 ow;
+                    ow.x = rho;
+                    ow.y = gs0;
+                    S.own[bC][t] = ow;
+                    S.gR[gC][5][t] = gs4;
+                } else {
+                    R4 oo;
+                    oo.x = g4;
+                    oo.y = rho;
+                    oo.z = gs0;
+                    oo.w = gs4;
+                    S.own[bC][1][t] = oo;
+                }
                 if (inD && (STEADY || (r >= y0 && r < y1))) Pdst[(size_t)r * pitch + gx] = Pn;
             }
         }
@@ -369,7 +573,24 @@ struct Sweep {
         }
 
         // ---- A(k): moments, EOS, psi
+        if constexpr (STG) {
+            wait_row(&S.mbar[fq], (mph >> fq) & 1u, &errbits);
+            mph ^= 1u << fq;
+        }
         R rho_a = R(1), rhod_a = R(0), jx_a = R(0), jy_a = R(0), psi_a = R(0), ir_a = R(1);
+        if constexpr (STG) {
+            if (doA && (STEADY || colvalid)) {
+                const R* fr = &S.fR[fq][0][sidx];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) fa[q] = fr[q * NT];
+                const R* gr = &S.gR[gq][0][sidx];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) ga[q] = gr[q * NT];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) fa[q] = R(0);
+            }
+        }
         if (doA && (STEADY || colvalid)) {
             rhod_a = ((fa[0] + fa[1]) + (fa[2] + fa[3])) + ((fa[4] + fa[5]) + (fa[6] + fa[7])) + fa[8];
             rho_a = rhod_a + rho_ref;
@@ -388,15 +609,25 @@ struct Sweep {
                 WR.rho[a0][t] = rho_a;
                 WR.T[a0][t] = T_a;
             }
-            R4 o0, o1;
-            o0.x = ga[0]; o0.y = ga[1]; o0.z = ga[2]; o0.w = ga[3];
-            o1.x = ga[4]; o1.y = rho_a; o1.z = pa; o1.w = TdpdT;
-            S.own[b0][0][t] = o0;
-            S.own[b0][1][t] = o1;
+            if constexpr (STG) {
+                R2 ow;
+                ow.x = rho_a;
+                ow.y = TdpdT;
+                S.own[b0][t] = ow;
+            } else {
+                R4 o0, o1;
+                o0.x = ga[0]; o0.y = ga[1]; o0.z = ga[2]; o0.w = ga[3];
+                o1.x = ga[4]; o1.y = rho_a; o1.z = pa; o1.w = TdpdT;
+                S.own[b0][0][t] = o0;
+                S.own[b0][1][t] = o1;
+            }
             // this unit's output rows only (steady iterations also load the
             // three rows above the segment)
             mass_acc += (inD && k >= y0 && k < y1) ? rho_a : R(0);
         }
+        // the g*_4 written over a staged P plane precedes the bulk copies that
+        // later refill that slot
+        if constexpr (STG) fence_proxy_async();
         __syncthreads();
 
         // ================= phase beta =================
@@ -404,8 +635,12 @@ struct Sweep {
         R fpn[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) fpn[q] = fa[q];
-        const int kwn = (pery && kw == ny - 1) ? 0 : kw + 1;
-        load_row(k + 1, kwn);
+        if constexpr (!STG) load_row(k + 1, kwn);
+        // staged form: every thread is past its wait for row k, so row k's
+        // mbarrier (and f slot) can take row k + 3
+        if constexpr (STG) {
+            if (k + 3 <= y1 + 3) arm_row(k + 3, fq);
+        }
 
         // ---- B(k-1): interaction force, velocity, D2Q9 MRT collision
         {
@@ -556,8 +791,22 @@ struct Sweep {
         {
             const int r = k - 4;
             if (STEADY || (r >= y0 && r < y1 && inD)) {
-                const R4 o0 = S.own[bD][0][t];
-                const R4 o1 = S.own[bD][1][t];
+                R4 o0, o1;
+                if constexpr (STG) {
+                    const R* gr = &S.gR[gD][0][sidx];
+                    o0.x = gr[0];
+                    o0.y = gr[NT];
+                    o0.z = gr[2 * NT];
+                    o0.w = gr[3 * NT];
+                    o1.x = gr[4 * NT];
+                    const R2 ow = S.own[bD][t];
+                    o1.y = ow.x;
+                    o1.z = ow.y;
+                    o1.w = S.gR[gD][5][t];
+                } else {
+                    o0 = S.own[bD][0][t];
+                    o1 = S.own[bD][1][t];
+                }
                 R go[5];
                 if (P.frozen_thermal) {
                     go[0] = o0.x; go[1] = o0.y; go[2] = o0.z; go[3] = o0.w; go[4] = o1.x;
@@ -576,7 +825,10 @@ struct Sweep {
                     R A2, A4;
                     if (vd) A2 = S.gs[a2][1][t];
                     else A2 = dirS ? twS2 - o1.w : o1.w;
-                    if (vu) A4 = S.own[bC][1][t].w;
+                    if (vu) {
+                        if constexpr (STG) A4 = S.gR[gC][5][t];
+                        else A4 = S.own[bC][1][t].w;
+                    }
                     else A4 = dirN ? twN2 - gsc[1 * NT] : gsc[1 * NT];
                     const R A0 = o1.z;
                     const R iC = f_rcp(o1.y * P.cv);
@@ -605,6 +857,9 @@ struct Sweep {
         irp = ir_a;
         b0 = b0 == 4 ? 0 : b0 + 1;
         kw = kwn;
+        gq = gq == 6 ? 0 : gq + 1;
+        fq = fq == 2 ? 0 : fq + 1;
+        kw2 = (pery && kw2 == ny - 1) ? 0 : kw2 + 1;
     }
 
     // general iteration with the rotating slots
@@ -620,12 +875,13 @@ struct Sweep {
     }
 };
 
-template <int PREC, int NT, bool UNIT>
+template <int PREC, int NT, bool UNIT, bool STG>
 __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
                                              const Phys<typename Types<PREC>::R>& P,
-                                             StepSmem<typename Types<PREC>::R, NT>& S,
-                                             WallRings<typename Types<PREC>::R, NT>& WR) {
-    Sweep<PREC, NT, UNIT> w(I, U, P, S, WR);
+                                             typename Sweep<PREC, NT, UNIT, STG>::SM& S,
+                                             WallRings<typename Types<PREC>::R, NT>& WR,
+                                             int& fq, unsigned& mph) {
+    Sweep<PREC, NT, UNIT, STG> w(I, U, P, S, WR, fq, mph);
     const int y0 = U.y0, y1 = U.y1;
     // iterations whose five stages are all active on rows with interior
     // neighbours take the steady form
@@ -645,6 +901,8 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
         w.template iter<true>(k + 2, 2, 1, 0);
     }
     for (; k <= y1 + 3; ++k) w.iter_general(k);
+    fq = w.fq;
+    mph = w.mph;
 
     if (w.errbits) atomicOr(&I.ctl->err, w.errbits);
     if (w.use_mass) {
@@ -664,13 +922,23 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
     }
 }
 
-template <int PREC, int NT, bool UNIT>
+template <int PREC, int NT, bool UNIT, bool STG>
 __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
     k_step(StepLaunch L, Phys<typename Types<PREC>::R> P) {
     typedef typename Types<PREC>::R R;
+    typedef typename Sweep<PREC, NT, UNIT, STG>::SM SM;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    StepSmem<R, NT>& S = *reinterpret_cast<StepSmem<R, NT>*>(smem_raw);
-    WallRings<R, NT>& WR = *reinterpret_cast<WallRings<R, NT>*>(smem_raw + sizeof(StepSmem<R, NT>));
+    SM& S = *reinterpret_cast<SM*>(smem_raw);
+    WallRings<R, NT>& WR = *reinterpret_cast<WallRings<R, NT>*>(smem_raw + sizeof(SM));
+    int fq = 0;
+    unsigned mph = 0;
+    if constexpr (STG) {
+        if (threadIdx.x == 0) {
+            for (int m = 0; m < 3; ++m) mbar_init(&S.mbar[m], 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
     for (;;) {
         if (threadIdx.x == 0) S.unit = (int)atomicAdd(&L.sched[0], 1u);
         __syncthreads();
@@ -678,7 +946,7 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
         __syncthreads();
         if (u >= L.n_units) break;
         const Unit U = L.units[u];
-        process_unit<PREC, NT, UNIT>(L.insts[U.inst], U, P, S, WR);
+        process_unit<PREC, NT, UNIT, STG>(L.insts[U.inst], U, P, S, WR, fq, mph);
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -707,52 +975,70 @@ static bool unit_rates(const PhysD& d) {
     return d.s_e == 1.0 && d.s_eps == 1.0 && d.s_q == 1.0 && d.vs3 == 1.0 && d.vs4 == 1.0;
 }
 
-template <int PREC, int NT>
+template <int PREC, int NT, bool STG>
 static size_t smem_for(bool walls) {
     typedef typename Types<PREC>::R R;
-    return sizeof(StepSmem<R, NT>) + (walls ? sizeof(WallRings<R, NT>) : 0);
+    typedef typename std::conditional<STG, StageSmem<R, NT>, StepSmem<R, NT>>::type SM;
+    return sizeof(SM) + (walls ? sizeof(WallRings<R, NT>) : 0);
 }
 
-template <int PREC, int NT, bool UNIT>
+template <int PREC, int NT, bool UNIT, bool STG>
 static int set_smem_attr() {
     static bool done = false;
     if (!done) {
-        if (cudaFuncSetAttribute(k_step<PREC, NT, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_for<PREC, NT>(true)) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_step<PREC, NT, UNIT, STG>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_for<PREC, NT, STG>(true)) != cudaSuccess)
             return -1;
         done = true;
     }
     return 0;
 }
 
-template <int PREC, int NT>
-static int launch_one(const StepLaunch& L, cudaStream_t st) {
+template <int PREC, int NT, bool STG>
+static int launch_form(const StepLaunch& L, cudaStream_t st) {
     typedef typename Types<PREC>::R R;
-    const size_t smem = smem_for<PREC, NT>(L.walls != 0);
+    const size_t smem = smem_for<PREC, NT, STG>(L.walls != 0);
     Phys<R> P = make_phys<R>(L.phys);
     if (unit_rates(L.phys)) {
-        if (set_smem_attr<PREC, NT, true>()) return -1;
-        k_step<PREC, NT, true><<<L.grid, NT, smem, st>>>(L, P);
+        if (set_smem_attr<PREC, NT, true, STG>()) return -1;
+        k_step<PREC, NT, true, STG><<<L.grid, NT, smem, st>>>(L, P);
     } else {
-        if (set_smem_attr<PREC, NT, false>()) return -1;
-        k_step<PREC, NT, false><<<L.grid, NT, smem, st>>>(L, P);
+        if (set_smem_attr<PREC, NT, false, STG>()) return -1;
+        k_step<PREC, NT, false, STG><<<L.grid, NT, smem, st>>>(L, P);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <int PREC, int NT>
-static int occ_one(int walls, int* ctas, size_t* smem_bytes) {
-    const size_t smem = smem_for<PREC, NT>(walls != 0);
-    if (set_smem_attr<PREC, NT, true>() || set_smem_attr<PREC, NT, false>()) return -1;
+static int launch_one(const StepLaunch& L, cudaStream_t st) {
+    if constexpr (PREC == 1) {
+        if (L.staged) return launch_form<PREC, NT, true>(L, st);
+    }
+    return launch_form<PREC, NT, false>(L, st);
+}
+
+template <int PREC, int NT, bool STG>
+static int occ_form(int walls, int* ctas, size_t* smem_bytes) {
+    const size_t smem = smem_for<PREC, NT, STG>(walls != 0);
+    if (set_smem_attr<PREC, NT, true, STG>() || set_smem_attr<PREC, NT, false, STG>()) return -1;
     int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<PREC, NT, true>, NT, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<PREC, NT, true, STG>, NT, smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<PREC, NT, false>, NT, smem) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<PREC, NT, false, STG>, NT, smem) !=
             cudaSuccess)
         return -1;
     *ctas = a < b ? a : b;
     *smem_bytes = smem;
     return 0;
+}
+
+template <int PREC, int NT>
+static int occ_one(int walls, int staged, int* ctas, size_t* smem_bytes) {
+    if constexpr (PREC == 1) {
+        if (staged) return occ_form<PREC, NT, true>(walls, ctas, smem_bytes);
+    }
+    return occ_form<PREC, NT, false>(walls, ctas, smem_bytes);
 }
 
 int step_launch(int prec, int threads, const StepLaunch& L, cudaStream_t st) {
@@ -761,20 +1047,30 @@ int step_launch(int prec, int threads, const StepLaunch& L, cudaStream_t st) {
         if (prec == 1) return launch_one<1, 128>(L, st);
         return launch_one<2, 128>(L, st);
     }
+    if (threads == 224) {
+        if (prec == 0) return launch_one<0, 224>(L, st);
+        if (prec == 1) return launch_one<1, 224>(L, st);
+        return launch_one<2, 224>(L, st);
+    }
     if (prec == 0) return launch_one<0, 256>(L, st);
     if (prec == 1) return launch_one<1, 256>(L, st);
     return launch_one<2, 256>(L, st);
 }
 
-int step_occupancy(int prec, int threads, int walls, int* ctas, size_t* smem) {
+int step_occupancy(int prec, int threads, int walls, int staged, int* ctas, size_t* smem) {
     if (threads == 128) {
-        if (prec == 0) return occ_one<0, 128>(walls, ctas, smem);
-        if (prec == 1) return occ_one<1, 128>(walls, ctas, smem);
-        return occ_one<2, 128>(walls, ctas, smem);
+        if (prec == 0) return occ_one<0, 128>(walls, staged, ctas, smem);
+        if (prec == 1) return occ_one<1, 128>(walls, staged, ctas, smem);
+        return occ_one<2, 128>(walls, staged, ctas, smem);
     }
-    if (prec == 0) return occ_one<0, 256>(walls, ctas, smem);
-    if (prec == 1) return occ_one<1, 256>(walls, ctas, smem);
-    return occ_one<2, 256>(walls, ctas, smem);
+    if (threads == 224) {
+        if (prec == 0) return occ_one<0, 224>(walls, staged, ctas, smem);
+        if (prec == 1) return occ_one<1, 224>(walls, staged, ctas, smem);
+        return occ_one<2, 224>(walls, staged, ctas, smem);
+    }
+    if (prec == 0) return occ_one<0, 256>(walls, staged, ctas, smem);
+    if (prec == 1) return occ_one<1, 256>(walls, staged, ctas, smem);
+    return occ_one<2, 256>(walls, staged, ctas, smem);
 }
 
 }  // namespace lbm

@@ -25,11 +25,13 @@ def run_oracle(case, steps):
     return s
 
 
-def run_gpu(case, steps, prec, tile=None, chunks=None):
+def run_gpu(case, steps, prec, tile=None, chunks=None, staged=None):
     import paper_2205_00686_gb300 as lbm
     d = lbm.Domain(case.nx, case.ny, case.params, case.bc, prec=prec)
     if tile:
         d.set_tile(*tile)
+    if staged is not None:
+        d.staged = staged
     d.init_fields(*case.fields())
     if chunks:
         for c in chunks:

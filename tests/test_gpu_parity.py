@@ -120,6 +120,57 @@ def test_tiles_give_identical_results():
         assert P.rel_err(ref[128][1], ref[th][1]) < 1e-6
 
 
+@pytest.mark.parametrize("name", ["periodic", "open_dirichlet", "wall_open_heater",
+                                  "two_walls_adiabatic", "open_x_walls_y", "periodic_x_open_y",
+                                  "open_x_periodic_y"])
+@pytest.mark.parametrize("size", [(36, 20), (64, 48), (250, 75), (200, 40), (17, 13)])
+def test_staged_rows_equal_register_rows(name, size):
+    """The FP32 step with its rows staged in shared memory by bulk copies does
+    the same arithmetic as the register-prefetch form: the populations agree
+    to FP32 rounding (separately compiled kernels may contract multiply-adds
+    differently), on single and multi-strip domains, ragged tails, windows
+    that wrap several times around a periodic axis, and every boundary kind.
+    Sizes the staged form cannot take (periodic x with nx % 4 != 0) are
+    refused with LBM_EINVAL and keep the register form."""
+    import paper_2205_00686_gb300 as lbm
+    bc = P.bc_variants()[name]
+    c = P.droplet_case(size[0], size[1], bc, gravity=2e-5)
+    perx = bc["flow"][0] == W.PERIODIC
+    if perx and size[0] % 4:
+        d = P.run_gpu(c, 0, "fp32")
+        assert not d.staged
+        with pytest.raises(lbm.LbmError) as e:
+            d.staged = True
+        assert e.value.code == lbm.LBM_EINVAL
+        return
+    for tile in [None, (224, 13), (256, 11)]:
+        a = P.run_gpu(c, 60, "fp32", tile=tile, staged=True, chunks=[1, 59])
+        b = P.run_gpu(c, 60, "fp32", tile=tile, staged=False, chunks=[1, 59])
+        assert a.staged and not b.staged
+        fa, ga, Pa = a.populations()
+        fb, gb, Pb = b.populations()
+        assert np.isfinite(fa).all() and np.isfinite(ga).all()
+        assert P.rel_err(fa, fb) < 1e-6 and P.rel_err(ga, gb) < 1e-6, (name, size, tile)
+        assert P.rel_err(Pa, Pb) < 1e-5, (name, size, tile)
+
+
+def test_staged_rows_match_oracle_fp32_1000_steps():
+    """The staged FP32 path against the FP64 oracle on the 64 x 64 droplet
+    (periodic, nx a multiple of 4) and a 250 x 75 open-x case, 1000 steps."""
+    c = W.static_droplet()
+    o = P.run_oracle(c, 1000)
+    g = P.run_gpu(c, 1000, "fp32", staged=True)
+    assert g.staged
+    fe = P.field_errors(g.get_rho_u_T(), o.fields())
+    assert max(fe.values()) <= TOL32, fe
+    c = P.droplet_case(250, 75, P.bc_variants()["open_dirichlet"], gravity=3e-5)
+    o = P.run_oracle(c, 300)
+    g = P.run_gpu(c, 300, "fp32", staged=True)
+    assert g.staged
+    fe = P.field_errors(g.get_rho_u_T(), o.fields())
+    assert fe["rho"] <= TOL32 and fe["T"] <= TOL32, fe
+
+
 def test_diagnostics_match_oracle():
     c = W.open_evaporation(96, 96, R=24)
     o = P.run_oracle(c, 100)
