@@ -253,6 +253,56 @@ def served_check(n_inst, steps, budget_gb=1.0):
             "sequential_single_domain_mlups": round(solo_mlups, 1)}
 
 
+def batched_check(n_inst, steps, peak, warmup=3):
+    """The batched population resident on the device: n_inst open-evaporation
+    domains with sides uniform in 64..512 attached to one batch and advanced
+    together, one persistent launch per step (CUDA graph replays).  Timed with
+    CUDA events on the batch stream, first with the default tile, then with
+    the tile lbm_batch_autotune picks on a shadow batch."""
+    import torch
+    import paper_2205_00686_gb300 as lbm
+    from paper_2205_00686_gb300 import workloads as W
+    cases = W.batch_instances(n_inst, steps=steps)
+    stream = torch.cuda.Stream()
+    b = lbm.Batch(stream=stream.cuda_stream)
+    doms = []
+    for c in cases:
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32", stream=stream.cuda_stream)
+        d.init_fields(*c.fields())
+        b.attach(d)
+        doms.append(d)
+    nodes = sum(c.nx * c.ny for c in cases)
+
+    def timed():
+        b.step(warmup)
+        b.sync()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        b.step(steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        if b.sync() != 0:
+            raise RuntimeError("batched leg: device error")
+        return ev0.elapsed_time(ev1) / 1e3
+
+    tile0 = b.tile()
+    t0 = timed()
+    tile = b.autotune(5)
+    t1 = timed()
+    out = {"instances": n_inst, "total_nodes": nodes, "steps": steps,
+           "mlups": round(nodes * steps / t1 / 1e6, 1),
+           "tile": [tile[0], tile[1]], "staged": tile[2],
+           "hbm_frac_of_measured": round(BYTES_PER_NODE["fp32"] * nodes * steps / t1 / 1e9 / peak, 4),
+           "default_tile": [tile0[0], tile0[1]], "default_staged": tile0[2],
+           "default_tile_mlups": round(nodes * steps / t0 / 1e6, 1)}
+    b.close()
+    for d in doms:
+        d.close()
+    return out
+
+
 def time_device(dom, steps, warmup, stream, torch, dist, world):
     dom.step(warmup)
     dom.sync()
@@ -400,6 +450,7 @@ def run_ours(args):
         extras["d3q19_d3q7"] = bench_3d(lbm, stream, torch, peak)
         extras["error_vs_fp64"] = accuracy_check()
         if not args.no_serve:
+            extras["batched"] = batched_check(args.serve_instances, 200, peak)
             extras["served"] = served_check(args.serve_instances, args.serve_steps)
 
     cpu = None

@@ -278,6 +278,16 @@ int lbm_batch_step(lbm_batch* b, int n);
  * the attached contexts (and records it in that context). */
 int lbm_batch_sync(lbm_batch* b);
 void lbm_batch_destroy(lbm_batch* b);
+/* Chooses the batch's tile (load path, threads, rows) by timing each
+ * candidate for steps_per_trial steps on a shadow batch: scratch domains of
+ * the members' sizes, precision, boundaries and parameters in a uniform
+ * state, so the members' states are untouched (the shadow needs as much
+ * device memory as the members, for the duration of the call).  The choice
+ * is kept while members attach and detach (staging drops out while some
+ * member cannot take it).  Without it a batch uses the lbm_create defaults
+ * with 64-row segments.  lbm_batch_get_tile reports the tile in use. */
+int lbm_batch_autotune(lbm_batch* b, int steps_per_trial);
+int lbm_batch_get_tile(const lbm_batch* b, int* threads, int* rows, int* staged);
 
 /* ---- launch configuration ------------------------------------------------ *
  * Tile of the fused step: a strip of (threads - 8) columns swept over a
@@ -288,19 +298,23 @@ int lbm_set_tile(lbm_ctx* ctx, int threads, int rows);
 int lbm_get_tile(const lbm_ctx* ctx, int* threads, int* rows);
 int lbm_autotune(lbm_ctx* ctx, int steps_per_trial);
 
-/* Load path of the fused FP32 step (no counterpart in the paper, which
+/* Load path of the fused FP32 / FP32_G16 step (no counterpart in the paper, which
  * prescribes no implementation).  on = 1: each row of f, g and P^{n-1} that a
  * tile needs is brought into shared memory by bulk asynchronous copies
- * (cp.async.bulk, completion tracked by an mbarrier) a full row ahead of its
+ * (cp.async.bulk, completion tracked by an mbarrier) two rows ahead of its
  * use; on = 0: each thread loads its own column a half row ahead into
- * registers.  The two paths compute identical results (same arithmetic in
- * the same order).  Staging needs FP32 storage and either open x edges or a
- * periodic x axis with nx a multiple of 4 (nx >= 32); lbm_create turns it on
- * where it is possible, lbm_autotune times both paths.  Returns LBM_EINVAL
+ * registers.  Both paths do the same arithmetic in the same order; results
+ * agree to rounding (the two kernels are compiled separately, so multiply-
+ * adds may be contracted differently).  Staging needs LBM_FP32 or LBM_FP32_G16 and either open x
+ * edges or a periodic x axis with nx >= 32 a multiple of 4 (LBM_FP32) or 8
+ * (LBM_FP32_G16); lbm_create turns it on (with a 224-thread tile) for
+ * wall-free domains wide enough for 216-column strips, lbm_autotune times
+ * both paths.  Returns LBM_EINVAL
  * when on = 1 is not possible, LBM_ESTATE for a context in a batch.  A
  * staged launch that waits more than about a second for a row reports
  * LBM_ETIMEOUT (sticky) instead of hanging.  lbm_get_staging returns 0 or 1
- * (LBM_EINVAL for NULL).  A batch stages when every member can. */
+ * (LBM_EINVAL for NULL).  A batch stages (224-thread tile) when every member
+ * can and has no walls, and its members are wide enough as a whole. */
 int lbm_set_staging(lbm_ctx* ctx, int on);
 int lbm_get_staging(const lbm_ctx* ctx);
 

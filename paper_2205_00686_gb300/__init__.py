@@ -37,7 +37,8 @@ ABI_FUNCTIONS = (
     "lbm_get_rho_u_T", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
     "lbm_step_count", "lbm_sync", "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
     "lbm_batch_create", "lbm_batch_attach", "lbm_batch_detach", "lbm_batch_size",
-    "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy", "lbm_set_tile", "lbm_get_tile",
+    "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy", "lbm_batch_autotune",
+    "lbm_batch_get_tile", "lbm_set_tile", "lbm_get_tile",
     "lbm_autotune", "lbm_set_staging", "lbm_get_staging", "lbm_diag_reduce_noalloc", "lbm_reconfigure", "lbm_contact_angle",
     "lbm_regions",
     # include/lbm3d.h
@@ -132,6 +133,9 @@ def lib():
             "lbm_batch_step": ([_vp, ctypes.c_int], ctypes.c_int),
             "lbm_batch_sync": ([_vp], ctypes.c_int),
             "lbm_batch_destroy": ([_vp], None),
+            "lbm_batch_autotune": ([_vp, ctypes.c_int], ctypes.c_int),
+            "lbm_batch_get_tile": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "lbm_set_tile": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "lbm_get_tile": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                              ctypes.c_int),
@@ -468,6 +472,18 @@ class Batch:
 
     def sync(self):
         return lib().lbm_batch_sync(self._h)
+
+    def autotune(self, steps_per_trial: int = 5):
+        """Times load path x threads x rows on a shadow batch of the members'
+        shapes (members untouched) and applies the fastest; returns tile()."""
+        _check(lib().lbm_batch_autotune(self._h, int(steps_per_trial)))
+        return self.tile()
+
+    def tile(self):
+        """(threads, rows, staged) of the batch's launches."""
+        t, r, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        lib().lbm_batch_get_tile(self._h, ctypes.byref(t), ctypes.byref(r), ctypes.byref(g))
+        return t.value, r.value, bool(g.value)
 
     def close(self):
         if getattr(self, "_h", None):

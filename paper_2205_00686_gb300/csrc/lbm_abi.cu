@@ -148,11 +148,12 @@ bool has_walls(const Inst& I) {
 // default load path and tile: bulk-copy staging on a 224-thread tile (two
 // CTAs per SM, two rows in flight per CTA) where the domains can take it,
 // have no walls (the wall rings would leave one CTA per SM) and are wide
-// enough that 216-column strips waste no more than 10 % more thread columns
-// than 120-column ones (the staged step is ~10 % faster per thread column on
-// 4096^2; a 64-wide domain fills 29 % of a 224-thread strip, 50 % of a
-// 128-thread one); otherwise the register-prefetch form on 128 threads
-// (four CTAs per SM)
+// enough that 216-column strips need no more thread columns than 120-column
+// ones (a 64-wide domain fills 29 % of a 224-thread strip, 50 % of a
+// 128-thread one; on the 512-domain mix with sides 64..512, 9 % more thread
+// columns already made the staged tile 12 % slower); otherwise the
+// register-prefetch form on 128 threads (four CTAs per SM).  lbm_autotune /
+// lbm_batch_autotune replace this guess by timed trials.
 long long strip_columns(int nx, int threads) {
     return (long long)((nx + threads - 9) / (threads - 8)) * threads;
 }
@@ -163,7 +164,7 @@ bool default_staged(const Inst* const* I, size_t n, int prec) {
         c224 += strip_columns(I[i]->nx, 224) * I[i]->ny;
         c128 += strip_columns(I[i]->nx, 128) * I[i]->ny;
     }
-    return n > 0 && 10 * c224 <= 11 * c128;
+    return n > 0 && c224 <= c128;
 }
 int default_threads(int staged) { return staged ? 224 : 128; }
 
@@ -222,6 +223,8 @@ struct lbm_batch {
     Unit* units = nullptr;
     unsigned* sched = nullptr;
     int n_units = 0, grid = 1, threads = 128, rows = 64, prec = -1, walls = 0, staged = 0;
+    // tile chosen by lbm_batch_autotune (kept across attach / detach)
+    int tuned = 0, t_threads = 128, t_rows = 64, t_staged = 0;
     PhysD phys;
     lbm_params params;
     cudaGraphExec_t graph = nullptr;
@@ -959,7 +962,9 @@ int lbm_set_staging(lbm_ctx* c, int on) {
     if (!c) return LBM_EINVAL;
     if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
     if (on && !stage_eligible(c->inst, c->prec))
-        return set_err(c, LBM_EINVAL, "bulk-copy staging needs FP32 and open x or nx % 4 == 0");
+        return set_err(c, LBM_EINVAL,
+                       "bulk-copy staging needs FP32 storage of f and open x, or periodic x "
+                       "with nx >= 32 a multiple of 4 (FP32 g) or 8 (FP16 g)");
     return ctx_apply_tile(c, c->threads, c->rows, on ? 1 : 0);
 }
 
@@ -1042,9 +1047,18 @@ static int batch_rebuild(lbm_batch* b) {
         ip.push_back(&b->members[i]->inst);
         if (has_walls(b->members[i]->inst)) b->walls = 1;
     }
-    // bulk-copy staging (224-thread tile) when the members as a whole take it
-    b->staged = default_staged(ip.data(), ip.size(), b->prec) ? 1 : 0;
-    b->threads = default_threads(b->staged);
+    if (b->tuned) {
+        // the autotuned tile; staging only while every member can take it
+        bool all = true;
+        for (const Inst* I : ip) all = all && stage_eligible(*I, b->prec);
+        b->threads = b->t_threads;
+        b->rows = b->t_rows;
+        b->staged = b->t_staged && all ? 1 : 0;
+    } else {
+        // bulk-copy staging (224-thread tile) when the members as a whole take it
+        b->staged = default_staged(ip.data(), ip.size(), b->prec) ? 1 : 0;
+        b->threads = default_threads(b->staged);
+    }
     for (size_t i = 0; i < b->members.size(); ++i) {
         build_units(b->members[i]->inst, (int)i, b->threads, std::min(b->rows, b->members[i]->ny), us);
     }
@@ -1157,6 +1171,87 @@ int lbm_batch_sync(lbm_batch* b) {
         if (c->sticky && first == LBM_OK) first = c->sticky;
     }
     return first;
+}
+
+int lbm_batch_get_tile(const lbm_batch* b, int* threads, int* rows, int* staged) {
+    if (!b) return LBM_EINVAL;
+    if (threads) *threads = b->threads;
+    if (rows) *rows = b->rows;
+    if (staged) *staged = b->staged;
+    return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int steps) {
+    if (!b || steps < 1) return LBM_EINVAL;
+    if (b->members.empty()) return LBM_OK;
+    cudaStreamSynchronize(b->stream);
+    // a shadow batch of scratch domains with the members' sizes, precision,
+    // boundaries and parameters in a uniform state: the members' states are
+    // untouched
+    std::vector<lbm_ctx*> sh;
+    lbm_batch* s = nullptr;
+    int rc = lbm_batch_create(nullptr, &s);
+    for (size_t i = 0; rc == LBM_OK && i < b->members.size(); ++i) {
+        const lbm_ctx* m = b->members[i];
+        lbm_ctx* c = nullptr;
+        rc = lbm_create(m->nx, m->ny, &m->params, &m->bc, m->prec, nullptr, nullptr, 0, &c);
+        if (rc) break;
+        sh.push_back(c);
+        const size_t N = (size_t)m->nx * m->ny;
+        std::vector<double> rho(N, m->inst.rho_ref > 0 ? m->inst.rho_ref : 1.0), z(N, 0.0),
+            T(N, m->inst.T_ref > 0 ? m->inst.T_ref : 0.09);
+        rc = lbm_init_fields(c, rho.data(), z.data(), z.data(), T.data());
+        if (rc == LBM_OK) rc = lbm_batch_attach(s, c);
+    }
+    int bt = b->threads, br = b->rows, bs = b->staged;
+    if (rc == LBM_OK) {
+        bool elig = true;
+        for (lbm_ctx* c : sh) elig = elig && stage_eligible(c->inst, c->prec);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        const int thr_c[3] = {128, 224, 256};
+        const int rows_c[5] = {16, 32, 64, 128, 256};
+        for (int si = 0; si < (elig ? 2 : 1); ++si)
+            for (int ti = 0; ti < 3; ++ti)
+                for (int ri = 0; ri < 5; ++ri) {
+                    const int staged = elig ? 1 - si : 0;
+                    s->tuned = 1;
+                    s->t_threads = thr_c[ti];
+                    s->t_rows = rows_c[ri];
+                    s->t_staged = staged;
+                    int ctas = 0;
+                    size_t smem = 0;
+                    if (step_occupancy(s->prec, thr_c[ti], s->walls, staged, &ctas, &smem) ||
+                        ctas < 1)
+                        continue;
+                    if (batch_rebuild(s) != LBM_OK) continue;
+                    if (lbm_batch_step(s, 2) != LBM_OK) continue;
+                    cudaEventRecord(e0, s->stream);
+                    lbm_batch_step(s, steps);
+                    cudaEventRecord(e1, s->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) {
+                        best = ms;
+                        bt = thr_c[ti];
+                        br = rows_c[ri];
+                        bs = staged;
+                    }
+                }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (s) lbm_batch_destroy(s);
+    for (lbm_ctx* c : sh) lbm_destroy(c);
+    if (rc) return rc;
+    b->tuned = 1;
+    b->t_threads = bt;
+    b->t_rows = br;
+    b->t_staged = bs;
+    return batch_rebuild(b);
 }
 
 void lbm_batch_destroy(lbm_batch* b) {

@@ -122,6 +122,9 @@ __device__ __forceinline__ float ld_st(const __half* p) { return __half2float(__
 __device__ __forceinline__ void st_st(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st_st(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st_st(__half* p, float v) { *p = __float2half_rn(v); }
+// a staged (shared-memory) storage value as arithmetic type
+__device__ __forceinline__ float st_val(float v) { return v; }
+__device__ __forceinline__ float st_val(__half v) { return __half2float(v); }
 
 // ---- arithmetic helpers (precision-generic) -------------------------------
 // FP64 keeps IEEE division and square root (parity with the FP64 oracle to
@@ -213,19 +216,20 @@ struct StepLaunch {
     unsigned* sched;   // [0] next unit, [1] finished CTAs
     int grid;
     int walls;         // some domain has a wall: the launch carries the wall rings
-    int staged;        // FP32 only: rows arrive by bulk copies (stage_eligible)
+    int staged;        // FP32 / FP16-g: rows arrive by bulk copies (stage_eligible)
     PhysD phys;
 };
 
-// The bulk-copy staged form of the FP32 step needs every copied row segment
-// to start on a 16-byte boundary: always true for open x edges (the copy of
-// the last strip is rounded up into the row's pitch padding), and for
-// periodic x when nx is a multiple of 4 (the wrapped pieces then start on
-// 4-column boundaries) and the window wraps at most a few times (nx >= 32).
+// The bulk-copy staged form (FP32 f and P; g in FP32 or FP16) needs every
+// copied row piece to start on a 16-byte boundary: always true for open x
+// edges (the copy of the last strip is rounded up into the row's pitch
+// padding), and for periodic x when the wrapped pieces start on 16-byte
+// column boundaries (nx a multiple of 4 for FP32 g, of 8 for FP16 g) and the
+// window wraps at most a few times (nx >= 32).
 inline bool stage_eligible(const Inst& I, int prec) {
-    if (prec != 1) return false;
+    if (prec != 1 && prec != 2) return false;
     if (I.flow[EW] != PERIODIC) return true;
-    return I.nx % 4 == 0 && I.nx >= 32;
+    return I.nx % (prec == 2 ? 8 : 4) == 0 && I.nx >= 32;
 }
 
 int step_launch(int prec, int threads, const StepLaunch& L, cudaStream_t st);

@@ -81,7 +81,8 @@ struct WallRings {
     R T[3][NT];
 };
 
-// Shared-memory layout of the bulk-copy staged form (FP32).  The rows of f,
+// Shared-memory layout of the bulk-copy staged form (FP32 state, g in FP32 or
+// FP16 storage).  The rows of f,
 // g and P^{n-1} arrive by cp.async.bulk (the copy engine of each SM, tracked
 // by one mbarrier per in-flight row) instead of per-thread loads, two rows
 // ahead of their use.  The step moves its bytes at the rate
@@ -91,11 +92,16 @@ struct WallRings {
 // rows in flight); g and P^{n-1} stay in their slots until stages C and D5 of
 // the row, four iterations later (seven slots), which replaces the
 // per-column ring of the register-prefetch form.  After stage C reads
-// P^{n-1} of a row, that plane holds the row's g*_4.
-template <class R, int NT>
+// P^{n-1} of a row, that plane holds the row's g*_4.  g rows are kept in
+// their storage type; FP16 rows are copied from the 8-column boundary at or
+// below the window start (16 bytes), so they carry 8 columns of slack.
+template <class TG>
+struct GPad { static constexpr int value = sizeof(TG) == 2 ? 8 : 0; };
+template <class R, class TG, int NT>
 struct StageSmem {
     R fR[3][9][NT];
-    R gR[7][6][NT];
+    R pR[7][NT];
+    TG gR[7][5][NT + GPad<TG>::value];
     R psi[3][NT];
     typename Vec2<R>::T u[3][NT];
     R fs[3][9][NT];
@@ -186,8 +192,9 @@ struct Sweep {
     typedef typename Types<PREC>::TG TG;
     typedef typename Vec2<R>::T R2;
     typedef typename Vec4<R>::T R4;
-    typedef typename std::conditional<STG, StageSmem<R, NT>, StepSmem<R, NT>>::type SM;
-    static_assert(!STG || PREC == 1, "the staged form is FP32 only");
+    typedef typename std::conditional<STG, StageSmem<R, TG, NT>, StepSmem<R, NT>>::type SM;
+    static_assert(!STG || PREC != 0, "the staged form is FP32 / FP16-g only");
+    static constexpr int NTG = NT + GPad<TG>::value;   // staged g row length
 
     const Inst& I;
     const Phys<R>& P;
@@ -219,8 +226,8 @@ struct Sweep {
     // f ring (of 3), and the phase parity each f mbarrier completes next
     // (bit m for mbarrier m; the f ring and the mbarriers carry over from
     // one unit to the next)
-    int X0w, sidx, gq, fq, kw2, scs;
-    unsigned mph, sbytes, rbytes;
+    int X0w, sidx, gq, fq, kw2, scs, X0g, goff, gcs;
+    unsigned mph, sbytes, gbytes, rbytes;
 
     __device__ __forceinline__ Sweep(const Inst& I_, const Unit& U, const Phys<R>& P_, SM& S_,
                                      WallRings<R, NT>& WR_, int fq0, unsigned mph0)
@@ -332,7 +339,14 @@ struct Sweep {
             scs = perx ? X0w : max(X0w, 0);
             const int sce = perx ? X0w + NT : ((min(X0w + NT, nx) + 3) & ~3);
             sbytes = (unsigned)((sce - scs) * (int)sizeof(R));
-            rbytes = 15u * sbytes;
+            // g rows: FP32 as f; FP16 from the 8-column boundary X0g <= X0w
+            constexpr int GA = 16 / (int)sizeof(TG);   // columns per 16 bytes
+            X0g = X0w & ~(GA - 1);
+            goff = X0w - X0g;
+            gcs = perx ? X0g : max(X0g, 0);
+            const int gce = perx ? X0g + NTG : ((min(X0g + NTG, nx) + GA - 1) & ~(GA - 1));
+            gbytes = (unsigned)((gce - gcs) * (int)sizeof(TG));
+            rbytes = 10u * sbytes + 5u * gbytes;
             // wrapped rows y0 - 3 (kw), y0 - 2, y0 - 1; iteration k queues the
             // copies of row k + 2 and arms row k + 3
             const int kwa = (pery && kw == ny - 1) ? 0 : kw + 1;
@@ -370,19 +384,27 @@ struct Sweep {
         if (pl >= 15) return;
         unsigned long long* mb = &S.mbar[fslot];
         const size_t rowoff = (size_t)kwr * pitch;
-        const R* src = pl < 9    ? (const R*)fsrc + (size_t)pl * plane + rowoff
-                       : pl < 14 ? (const R*)gsrc + (size_t)(pl - 9) * plane + rowoff
-                                 : Psrc + rowoff;
-        R* dst = pl < 9 ? &S.fR[fslot][pl][0] : &S.gR[gslot][pl < 14 ? pl - 9 : 5][0];
+        // byte addresses of the plane row's column 0 in global and staged
+        // memory, the element size and the window of this plane
+        const bool isg = pl >= 9 && pl < 14;
+        const char* src = pl < 9 ? (const char*)(fsrc + (size_t)pl * plane + rowoff)
+                          : isg  ? (const char*)(gsrc + (size_t)(pl - 9) * plane + rowoff)
+                                 : (const char*)(Psrc + rowoff);
+        char* dst = pl < 9 ? (char*)&S.fR[fslot][pl][0]
+                    : isg  ? (char*)&S.gR[gslot][pl - 9][0]
+                           : (char*)&S.pR[gslot][0];
+        const int es = isg ? (int)sizeof(TG) : (int)sizeof(R);
+        const int w0 = isg ? X0g : X0w;
         if (!perx) {
-            bulk_g2s(dst + (scs - X0w), src + scs, sbytes, mb);
+            const int cs = isg ? gcs : scs;
+            bulk_g2s(dst + (cs - w0) * es, src + (size_t)cs * es, isg ? gbytes : sbytes, mb);
         } else {
-            int c = X0w;
-            const int end = X0w + NT;
+            int c = w0;
+            const int end = w0 + (isg ? NTG : NT);
             while (c < end) {
                 const int wc = wrapi(c, nx);
                 const int n = min(end - c, nx - wc);
-                bulk_g2s(dst + (c - X0w), src + wc, (unsigned)(n * sizeof(R)), mb);
+                bulk_g2s(dst + (c - w0) * es, src + (size_t)wc * es, (unsigned)(n * es), mb);
                 c += n;
             }
         }
@@ -437,13 +459,13 @@ struct Sweep {
             if (STEADY || (r >= y0 - 1 && r < y1 + 1 && rowvalid(r) && inC)) {
                 R g0, g1, g2, g3, g4, rho, Pp, TdpdT;
                 if constexpr (STG) {
-                    const R* gr = &S.gR[gC][0][sidx];
-                    g0 = gr[0];
-                    g1 = gr[NT];
-                    g2 = gr[2 * NT];
-                    g3 = gr[3 * NT];
-                    g4 = gr[4 * NT];
-                    Pp = gr[5 * NT];
+                    const TG* gr = &S.gR[gC][0][sidx + goff];
+                    g0 = st_val(gr[0]);
+                    g1 = st_val(gr[NTG]);
+                    g2 = st_val(gr[2 * NTG]);
+                    g3 = st_val(gr[3 * NTG]);
+                    g4 = st_val(gr[4 * NTG]);
+                    Pp = S.pR[gC][sidx];
                     const R2 ow = S.own[bC][t];
                     rho = ow.x;
                     TdpdT = ow.y;
@@ -528,7 +550,7 @@ struct Sweep {
                     ow.x = rho;
                     ow.y = gs0;
                     S.own[bC][t] = ow;
-                    S.gR[gC][5][t] = gs4;
+                    S.pR[gC][t] = gs4;
                 } else {
                     R4 oo;
                     oo.x = g4;
@@ -583,9 +605,9 @@ struct Sweep {
                 const R* fr = &S.fR[fq][0][sidx];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) fa[q] = fr[q * NT];
-                const R* gr = &S.gR[gq][0][sidx];
+                const TG* gr = &S.gR[gq][0][sidx + goff];
 #pragma unroll
-                for (int q = 0; q < 5; ++q) ga[q] = gr[q * NT];
+                for (int q = 0; q < 5; ++q) ga[q] = st_val(gr[q * NTG]);
             } else {
 #pragma unroll
                 for (int q = 0; q < 9; ++q) fa[q] = R(0);
@@ -793,16 +815,16 @@ struct Sweep {
             if (STEADY || (r >= y0 && r < y1 && inD)) {
                 R4 o0, o1;
                 if constexpr (STG) {
-                    const R* gr = &S.gR[gD][0][sidx];
-                    o0.x = gr[0];
-                    o0.y = gr[NT];
-                    o0.z = gr[2 * NT];
-                    o0.w = gr[3 * NT];
-                    o1.x = gr[4 * NT];
+                    const TG* gr = &S.gR[gD][0][sidx + goff];
+                    o0.x = st_val(gr[0]);
+                    o0.y = st_val(gr[NTG]);
+                    o0.z = st_val(gr[2 * NTG]);
+                    o0.w = st_val(gr[3 * NTG]);
+                    o1.x = st_val(gr[4 * NTG]);
                     const R2 ow = S.own[bD][t];
                     o1.y = ow.x;
                     o1.z = ow.y;
-                    o1.w = S.gR[gD][5][t];
+                    o1.w = S.pR[gD][t];
                 } else {
                     o0 = S.own[bD][0][t];
                     o1 = S.own[bD][1][t];
@@ -826,7 +848,7 @@ struct Sweep {
                     if (vd) A2 = S.gs[a2][1][t];
                     else A2 = dirS ? twS2 - o1.w : o1.w;
                     if (vu) {
-                        if constexpr (STG) A4 = S.gR[gC][5][t];
+                        if constexpr (STG) A4 = S.pR[gC][t];
                         else A4 = S.own[bC][1][t].w;
                     }
                     else A4 = dirN ? twN2 - gsc[1 * NT] : gsc[1 * NT];
@@ -978,7 +1000,8 @@ static bool unit_rates(const PhysD& d) {
 template <int PREC, int NT, bool STG>
 static size_t smem_for(bool walls) {
     typedef typename Types<PREC>::R R;
-    typedef typename std::conditional<STG, StageSmem<R, NT>, StepSmem<R, NT>>::type SM;
+    typedef typename Types<PREC>::TG TG;
+    typedef typename std::conditional<STG, StageSmem<R, TG, NT>, StepSmem<R, NT>>::type SM;
     return sizeof(SM) + (walls ? sizeof(WallRings<R, NT>) : 0);
 }
 
@@ -1012,7 +1035,7 @@ static int launch_form(const StepLaunch& L, cudaStream_t st) {
 
 template <int PREC, int NT>
 static int launch_one(const StepLaunch& L, cudaStream_t st) {
-    if constexpr (PREC == 1) {
+    if constexpr (PREC != 0) {
         if (L.staged) return launch_form<PREC, NT, true>(L, st);
     }
     return launch_form<PREC, NT, false>(L, st);
@@ -1035,7 +1058,7 @@ static int occ_form(int walls, int* ctas, size_t* smem_bytes) {
 
 template <int PREC, int NT>
 static int occ_one(int walls, int staged, int* ctas, size_t* smem_bytes) {
-    if constexpr (PREC == 1) {
+    if constexpr (PREC != 0) {
         if (staged) return occ_form<PREC, NT, true>(walls, ctas, smem_bytes);
     }
     return occ_form<PREC, NT, false>(walls, ctas, smem_bytes);

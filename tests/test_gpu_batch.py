@@ -177,3 +177,41 @@ def test_batched_population_sample_matches_oracle():
         assert max(fe.values()) <= 1e-12, (c.name, fe)
         d.close()
     b.close()
+
+
+def test_batch_autotune_leaves_members_untouched():
+    """lbm_batch_autotune times its candidates on a shadow batch: the members'
+    populations and step counters are unchanged by it, the chosen tile is one
+    of the candidates, and stepping on with it gives each domain its solo
+    result (to FP32 rounding: the tile may select another kernel
+    instantiation than the solo run's)."""
+    import paper_2205_00686_gb300 as lbm
+    v = P.bc_variants()
+    cases = [P.droplet_case(nx, ny, v[name], seed=31 + i)
+             for i, (nx, ny, name) in enumerate([(600, 90, "open_dirichlet"),
+                                                 (256, 128, "periodic"),
+                                                 (130, 70, "open_x_periodic_y")])]
+    b = lbm.Batch()
+    doms = []
+    for c in cases:
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+        d.init_fields(*c.fields())
+        b.attach(d)
+        doms.append(d)
+    b.step(10)
+    assert b.sync() == 0
+    before = [d.populations() for d in doms]
+    threads, rows, staged = b.autotune(2)
+    assert threads in (128, 224, 256) and rows in (16, 32, 64, 128, 256)
+    for d, pb in zip(doms, before):
+        assert d.step_count == 10
+        for a, r in zip(d.populations(), pb):
+            assert np.array_equal(a, r)
+    b.step(30)
+    assert b.sync() == 0
+    for c, d in zip(cases, doms):
+        f, g, Pp = d.populations()
+        fs, gs, Ps = solo(c, 40, "fp32")
+        assert P.rel_err(f, fs) < 1e-6 and P.rel_err(g, gs) < 1e-6, (c.name, threads, rows, staged)
+        assert d.step_count == 40
+    b.close()
