@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--serve-steps", type=int, default=500)
     ap.add_argument("--size", type=int, default=NX,
                     help="domain side (default 4096; smaller sides for profiler captures)")
+    ap.add_argument("--ny", type=int, default=None,
+                    help="domain height (default: the side; profiler captures on wide, short domains)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "fp32_g16"],
                     help="precision of the timed domain (profiler captures; the metric is FP32)")
     ap.add_argument("--only-3d", type=int, default=0, metavar="N",
@@ -172,9 +174,10 @@ class ClockSampler:
                 "samples": len(sms), "power_w_max": max(pw) if pw else None}
 
 
-def make_case(n=NX):
+def make_case(n=NX, ny=None):
     from paper_2205_00686_gb300 import workloads as W
-    return W.open_evaporation(n, n, R=640.0 * n / 4096.0, steps=0)
+    ny = n if ny is None else ny
+    return W.open_evaporation(n, ny, R=640.0 * min(n, ny) / 4096.0, steps=0)
 
 
 def cpu_baseline(sample_n=1024, sample_steps=60):
@@ -359,7 +362,7 @@ def run_ours(args):
     if rank == 0 or world > 1:
         _build.build()
     stream = torch.cuda.Stream()
-    case = make_case(args.size)
+    case = make_case(args.size, args.ny)
     N = case.nx * case.ny
 
     dom = lbm.Domain(case.nx, case.ny, case.params, case.bc, prec=args.prec,
@@ -464,7 +467,7 @@ def run_ours(args):
         "dtype": {"fp32": "f32", "fp64": "f64", "fp32_g16": "f32 (g stored f16)"}[args.prec],
         "data": "synthetic",
         "config": {"workload": "droplet evaporation, open outflow, Dirichlet 0.95Tc edges, "
-                               "R=%g, %dx%d, %s fused step" % (640.0 * case.nx / 4096.0,
+                               "R=%g, %dx%d, %s fused step" % (640.0 * min(case.nx, case.ny) / 4096.0,
                                                                case.nx, case.ny, args.prec.upper()),
                    "nx": case.nx, "ny": case.ny,
                    "l2": "inputs larger than L2 (%.2f GiB state)"

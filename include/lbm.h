@@ -291,7 +291,7 @@ int lbm_batch_get_tile(const lbm_batch* b, int* threads, int* rows, int* staged)
 
 /* ---- launch configuration ------------------------------------------------ *
  * Tile of the fused step: a strip of (threads - 8) columns swept over a
- * segment of `rows` rows.  threads is 128, 224 or 256; rows >= 1.  The autotuner
+ * segment of `rows` rows.  threads is 128, 192, 224 or 256; rows >= 1.  The autotuner
  * times the candidates on a scratch domain of the same size and precision
  * and applies the fastest; its choice is cached per (precision, size). */
 int lbm_set_tile(lbm_ctx* ctx, int threads, int rows);

@@ -168,18 +168,23 @@ bool default_staged(const Inst* const* I, size_t n, int prec) {
 }
 int default_threads(int staged) { return staged ? 224 : 128; }
 
-// default segment height: the tallest of 256, 128, 64, ... rows (each
-// segment re-sweeps 6 halo rows) that still gives the persistent grid at
-// least one unit per resident CTA; never below 8
+// default segment height: the work units of a launch should fill the
+// persistent grid in whole waves (one unit per resident CTA; a second, partial
+// wave doubles the time of the CTAs that take it), so take the most segments
+// per strip that keep strips x segments within one wave, and the rows that
+// gives; never below 8
+int wave_rows(int ny, long long strips, long long slots, int waves) {
+    const long long S = std::max<long long>(1, (long long)waves * slots / strips);
+    return (int)std::max<long long>(1, std::min<long long>(ny, std::max<long long>(8, (ny + S - 1) / S)));
+}
+
 int default_rows(int prec, int threads, int walls, int staged, int nx, int ny) {
     int ctas = 1;
     size_t smem = 0;
     step_occupancy(prec, threads, walls, staged, &ctas, &smem);
     const long long slots = (long long)std::max(ctas, 1) * num_sms();
-    const int strips = (nx + threads - 9) / (threads - 8);
-    int rows = 256;
-    while (rows > 8 && (long long)strips * ((ny + rows - 1) / rows) < slots) rows /= 2;
-    return std::max(1, std::min(rows, ny));
+    const long long strips = (nx + threads - 9) / (threads - 8);
+    return wave_rows(ny, strips, slots, 1);
 }
 
 }  // namespace
@@ -953,7 +958,8 @@ int lbm_regions(lbm_ctx* c, double threshold, int below, int* labels, lbm_region
 
 // ---- tile / autotune ------------------------------------------------------
 int lbm_set_tile(lbm_ctx* c, int threads, int rows) {
-    if (!c || (threads != 128 && threads != 224 && threads != 256) || rows < 1) return LBM_EINVAL;
+    if (!c || (threads != 128 && threads != 192 && threads != 224 && threads != 256) || rows < 1)
+        return LBM_EINVAL;
     if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
     return ctx_apply_tile(c, threads, std::min(rows, c->ny), c->staged);
 }
@@ -998,15 +1004,28 @@ int lbm_autotune(lbm_ctx* c, int steps) {
     cudaEventCreate(&e1);
     float best = 1e30f;
     int bt = c->threads, br = c->rows, bs = c->staged;
-    const int thr_c[3] = {128, 224, 256};
-    const int rows_c[6] = {16, 32, 64, 128, 256, 512};
+    const int thr_c[4] = {128, 192, 224, 256};
     const int n_paths = stage_eligible(c->inst, c->prec) ? 2 : 1;
     for (int si = 0; si < n_paths; ++si)
-        for (int ti = 0; ti < 3; ++ti)
-            for (int ri = 0; ri < 6; ++ri) {
-                int rows = std::min(rows_c[ri], c->ny);
-                if (ri > 0 && rows_c[ri - 1] >= c->ny) continue;
-                const int staged = n_paths == 2 ? 1 - si : 0;
+        for (int ti = 0; ti < 4; ++ti) {
+            const int staged = n_paths == 2 ? 1 - si : 0;
+            // powers of two, and the heights that fill the grid in 1, 2, 3
+            // whole waves
+            std::vector<int> rows_c = {16, 32, 64, 128, 256, 512};
+            {
+                int ctas = 0;
+                size_t smem = 0;
+                if (step_occupancy(c->prec, thr_c[ti], has_walls(c->inst), staged, &ctas, &smem) ||
+                    ctas < 1)
+                    continue;
+                const long long strips = (c->nx + thr_c[ti] - 9) / (thr_c[ti] - 8);
+                for (int w = 1; w <= 3; ++w)
+                    rows_c.push_back(wave_rows(c->ny, strips, (long long)ctas * num_sms(), w));
+            }
+            std::sort(rows_c.begin(), rows_c.end());
+            for (int& r : rows_c) r = std::min(r, c->ny);
+            rows_c.erase(std::unique(rows_c.begin(), rows_c.end()), rows_c.end());
+            for (int rows : rows_c) {
                 if (ctx_apply_tile(s, thr_c[ti], rows, staged)) continue;
                 lbm_step(s, 2);
                 cudaEventRecord(e0, s->stream);
@@ -1022,6 +1041,7 @@ int lbm_autotune(lbm_ctx* c, int steps) {
                     bs = staged;
                 }
             }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     lbm_destroy(s);
@@ -1211,10 +1231,10 @@ int lbm_batch_autotune(lbm_batch* b, int steps) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f;
-        const int thr_c[3] = {128, 224, 256};
+        const int thr_c[4] = {128, 192, 224, 256};
         const int rows_c[5] = {16, 32, 64, 128, 256};
         for (int si = 0; si < (elig ? 2 : 1); ++si)
-            for (int ti = 0; ti < 3; ++ti)
+            for (int ti = 0; ti < 4; ++ti)
                 for (int ri = 0; ri < 5; ++ri) {
                     const int staged = elig ? 1 - si : 0;
                     s->tuned = 1;

@@ -27,13 +27,13 @@
 //
 // Two load paths feed stage A.  In the register-prefetch form each thread
 // loads its column of row k + 1 into registers during phase beta of
-// iteration k.  In the staged form (FP32) the rows arrive in shared memory by
-// bulk asynchronous copies (cp.async.bulk, one mbarrier per row in flight),
-// issued two iterations ahead of their use, and g and P^{n-1} stay in their
-// staging slots until stages C and D5 have used them.  A bandwidth-bound
-// sweep moves (bytes in flight per SM) / (loaded HBM latency); one row per
-// thread in registers caps that at about 30 KB per SM, two staged rows per
-// CTA of the 224-thread tile (two CTAs per SM) double it.
+// iteration k.  In the staged form (FP32 f) the rows arrive in shared memory
+// by bulk asynchronous copies (cp.async.bulk, one mbarrier per row in
+// flight), issued two or three iterations ahead of their use (Ahead<NT>), and
+// g and P^{n-1} stay in their staging slots until stages C and D5 have used
+// them.  A bandwidth-bound sweep moves (bytes in flight per SM) / (loaded HBM
+// latency); one row per thread in registers caps that at about 30 KB per SM,
+// two staged rows per CTA of the 224-thread tile (two CTAs per SM) double it.
 //
 // The CTAs are persistent and pull (domain, strip, segment) units from an
 // atomic counter, so one launch serves one domain or hundreds of domains of
@@ -97,17 +97,23 @@ struct WallRings {
 // below the window start (16 bytes), so they carry 8 columns of slack.
 template <class TG>
 struct GPad { static constexpr int value = sizeof(TG) == 2 ? 8 : 0; };
+// rows in flight of the staged form: three on the narrower tiles (their
+// shared memory leaves room: 128 threads -> 3 CTAs, 192 -> 2 CTAs per SM),
+// two on 224 and 256 threads
+template <int NT>
+struct Ahead { static constexpr int value = NT <= 192 ? 3 : 2; };
 template <class R, class TG, int NT>
 struct StageSmem {
-    R fR[3][9][NT];
-    R pR[7][NT];
-    TG gR[7][5][NT + GPad<TG>::value];
+    static constexpr int D = Ahead<NT>::value;
+    R fR[D + 1][9][NT];
+    R pR[D + 5][NT];
+    TG gR[D + 5][5][NT + GPad<TG>::value];
     R psi[3][NT];
     typename Vec2<R>::T u[3][NT];
     R fs[3][9][NT];
     R gs[3][3][NT];
     typename Vec2<R>::T own[5][NT];   // rho, then T (dp/dT)_rho -> g*_0 after stage C
-    unsigned long long mbar[3];
+    unsigned long long mbar[D + 1];
     double red[NT / 32];
     int unit;
 };
@@ -195,6 +201,8 @@ struct Sweep {
     typedef typename std::conditional<STG, StageSmem<R, TG, NT>, StepSmem<R, NT>>::type SM;
     static_assert(!STG || PREC != 0, "the staged form is FP32 / FP16-g only");
     static constexpr int NTG = NT + GPad<TG>::value;   // staged g row length
+    static constexpr int DA = Ahead<NT>::value;        // staged rows in flight
+    static constexpr int NF = DA + 1, NGS = DA + 5;    // f and g/P ring slots
 
     const Inst& I;
     const Phys<R>& P;
@@ -347,17 +355,27 @@ struct Sweep {
             const int gce = perx ? X0g + NTG : ((min(X0g + NTG, nx) + GA - 1) & ~(GA - 1));
             gbytes = (unsigned)((gce - gcs) * (int)sizeof(TG));
             rbytes = 10u * sbytes + 5u * gbytes;
-            // wrapped rows y0 - 3 (kw), y0 - 2, y0 - 1; iteration k queues the
-            // copies of row k + 2 and arms row k + 3
-            const int kwa = (pery && kw == ny - 1) ? 0 : kw + 1;
-            kw2 = (pery && kwa == ny - 1) ? 0 : kwa + 1;
-            const int f1 = fq == 2 ? 0 : fq + 1, f2 = f1 == 2 ? 0 : f1 + 1;
-            arm_row(y0 - 3, fq);
-            arm_row(y0 - 2, f1);
-            arm_row(y0 - 1, f2);
+            // iteration k queues the copies of row k + DA and arms row
+            // k + DA + 1
+            // rows y0 - 3 .. y0 - 3 + DA armed, the first DA of them
+            // issued; kw2 ends as the wrapped row y0 - 3 + DA
+            {
+                int fs = fq;
+                for (int j = 0; j <= DA; ++j) {
+                    arm_row(y0 - 3 + j, fs);
+                    fs = fs == NF - 1 ? 0 : fs + 1;
+                }
+            }
             __syncthreads();
-            issue_row(y0 - 3, kw, 0, fq);
-            issue_row(y0 - 2, kwa, 1, f1);
+            {
+                int fs = fq, kr = kw;
+                for (int j = 0; j < DA; ++j) {
+                    issue_row(y0 - 3 + j, kr, j, fs);
+                    fs = fs == NF - 1 ? 0 : fs + 1;
+                    kr = (pery && kr == ny - 1) ? 0 : kr + 1;
+                }
+                kw2 = kr;
+            }
         } else {
             load_row(y0 - 3, kw);
         }
@@ -441,14 +459,15 @@ struct Sweep {
         const int bD = b0 >= 4 ? b0 - 4 : b0 + 1;   // slot5(k - 4)
         const int kwn = (pery && kw == ny - 1) ? 0 : kw + 1;
         // staged form: g/P slots of rows k - 3 and k - 4; the copies of row
-        // k + 2 go out now, two iterations before stage A needs them (the f
+        // k + DA go out now, DA iterations before stage A needs them (the f
         // slot they fill held row k - 1, the g/P slot row k - 5: both were
         // last read before the previous iteration's closing barrier)
-        const int gC = gq >= 3 ? gq - 3 : gq + 4;
-        const int gD = gq >= 4 ? gq - 4 : gq + 3;
+        const int gC = gq >= 3 ? gq - 3 : gq + NGS - 3;
+        const int gD = gq >= 4 ? gq - 4 : gq + NGS - 4;
         if constexpr (STG) {
-            if (k + 2 <= y1 + 3)
-                issue_row(k + 2, kw2, gq >= 5 ? gq - 5 : gq + 2, fq == 0 ? 2 : fq - 1);
+            if (k + DA <= y1 + 3)
+                issue_row(k + DA, kw2, gq + DA >= NGS ? gq + DA - NGS : gq + DA,
+                          fq == 0 ? NF - 1 : fq - 1);
         }
         // ================= phase alpha =================
         const bool doA = STEADY || (k < y1 + 3 && rowvalid(k));
@@ -661,7 +680,7 @@ struct Sweep {
         // staged form: every thread is past its wait for row k, so row k's
         // mbarrier (and f slot) can take row k + 3
         if constexpr (STG) {
-            if (k + 3 <= y1 + 3) arm_row(k + 3, fq);
+            if (k + DA + 1 <= y1 + 3) arm_row(k + DA + 1, fq);
         }
 
         // ---- B(k-1): interaction force, velocity, D2Q9 MRT collision
@@ -879,8 +898,8 @@ struct Sweep {
         irp = ir_a;
         b0 = b0 == 4 ? 0 : b0 + 1;
         kw = kwn;
-        gq = gq == 6 ? 0 : gq + 1;
-        fq = fq == 2 ? 0 : fq + 1;
+        gq = gq == NGS - 1 ? 0 : gq + 1;
+        fq = fq == NF - 1 ? 0 : fq + 1;
         kw2 = (pery && kw2 == ny - 1) ? 0 : kw2 + 1;
     }
 
@@ -956,7 +975,7 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
     unsigned mph = 0;
     if constexpr (STG) {
         if (threadIdx.x == 0) {
-            for (int m = 0; m < 3; ++m) mbar_init(&S.mbar[m], 1);
+            for (int m = 0; m <= Ahead<NT>::value; ++m) mbar_init(&S.mbar[m], 1);
             mbar_init_fence();
         }
         __syncthreads();
@@ -1070,6 +1089,11 @@ int step_launch(int prec, int threads, const StepLaunch& L, cudaStream_t st) {
         if (prec == 1) return launch_one<1, 128>(L, st);
         return launch_one<2, 128>(L, st);
     }
+    if (threads == 192) {
+        if (prec == 0) return launch_one<0, 192>(L, st);
+        if (prec == 1) return launch_one<1, 192>(L, st);
+        return launch_one<2, 192>(L, st);
+    }
     if (threads == 224) {
         if (prec == 0) return launch_one<0, 224>(L, st);
         if (prec == 1) return launch_one<1, 224>(L, st);
@@ -1085,6 +1109,11 @@ int step_occupancy(int prec, int threads, int walls, int staged, int* ctas, size
         if (prec == 0) return occ_one<0, 128>(walls, staged, ctas, smem);
         if (prec == 1) return occ_one<1, 128>(walls, staged, ctas, smem);
         return occ_one<2, 128>(walls, staged, ctas, smem);
+    }
+    if (threads == 192) {
+        if (prec == 0) return occ_one<0, 192>(walls, staged, ctas, smem);
+        if (prec == 1) return occ_one<1, 192>(walls, staged, ctas, smem);
+        return occ_one<2, 192>(walls, staged, ctas, smem);
     }
     if (threads == 224) {
         if (prec == 0) return occ_one<0, 224>(walls, staged, ctas, smem);

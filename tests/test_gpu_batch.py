@@ -202,7 +202,7 @@ def test_batch_autotune_leaves_members_untouched():
     assert b.sync() == 0
     before = [d.populations() for d in doms]
     threads, rows, staged = b.autotune(2)
-    assert threads in (128, 224, 256) and rows in (16, 32, 64, 128, 256)
+    assert threads in (128, 192, 224, 256) and rows in (16, 32, 64, 128, 256)
     for d, pb in zip(doms, before):
         assert d.step_count == 10
         for a, r in zip(d.populations(), pb):

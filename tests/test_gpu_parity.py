@@ -147,7 +147,7 @@ def test_staged_rows_equal_register_rows(name, size, prec):
         assert e.value.code == lbm.LBM_EINVAL
         return
     tol = 1e-6 if prec == "fp32" else 2e-3
-    for tile in [None, (224, 13), (256, 11)]:
+    for tile in [None, (192, 10), (224, 13), (256, 11)]:
         a = P.run_gpu(c, 60, prec, tile=tile, staged=True, chunks=[1, 59])
         b = P.run_gpu(c, 60, prec, tile=tile, staged=False, chunks=[1, 59])
         assert a.staged and not b.staged
