@@ -256,6 +256,38 @@ def served_check(n_inst, steps, budget_gb=1.0):
             "sequential_single_domain_mlups": round(solo_mlups, 1)}
 
 
+def d2_law_check(steps=160000, every=8000, t_fit=32000):
+    """The D^2 law of Section 4.1 (200^2 box, D0 = 60 at 0.86 T_c, periodic
+    flow, edges held at T_c): the evaporation constant kappa from a straight
+    line fit of (D / D0)^2 against t after the initial transient, in FP32 and
+    in FP64, with the fit's R^2."""
+    import paper_2205_00686_gb300 as lbm
+    from paper_2205_00686_gb300 import workloads as W
+    out = {"setup": "Section 4.1: 200x200, D0=60 at 0.86Tc, periodic flow, T=Tc on the edges",
+           "steps": steps, "fit_from_step": t_fit}
+    for prec in ("fp32", "fp64"):
+        c = W.d2_droplet(200, D0=60.0, T_g=1.0)
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec=prec)
+        d.init_fields(*c.fields())
+        D0 = d.diagnostics(c.rho_l, c.rho_g)["diameter"]
+        t, y = [], []
+        for k in range(every, steps + 1, every):
+            d.step(every)
+            if k >= t_fit:
+                t.append(k)
+                y.append((d.diagnostics(c.rho_l, c.rho_g)["diameter"] / D0) ** 2)
+        d.close()
+        t, y = np.array(t, float), np.array(y)
+        A = np.vstack([t, np.ones_like(t)]).T
+        coef = np.linalg.lstsq(A, y, rcond=None)[0]
+        r2 = 1.0 - ((y - A @ coef) ** 2).sum() / ((y - y.mean()) ** 2).sum()
+        out["kappa_" + prec] = float("%.5g" % -coef[0])
+        out["r2_" + prec] = round(float(r2), 5)
+        out["d2_ratio_end_" + prec] = round(float(y[-1]), 4)
+    out["kappa_rel_diff_fp32_vs_fp64"] = float("%.3g" % abs(out["kappa_fp32"] / out["kappa_fp64"] - 1))
+    return out
+
+
 def batched_check(n_inst, steps, peak, warmup=3):
     """The batched population resident on the device: n_inst open-evaporation
     domains with sides uniform in 64..512 attached to one batch and advanced
@@ -451,6 +483,7 @@ def run_ours(args):
                               "hbm_frac_of_measured": round(BYTES_PER_NODE["fp32_g16"] * N / (tg / args.steps) / 1e9 / peak, 4)}
         dg.close()
         extras["d3q19_d3q7"] = bench_3d(lbm, stream, torch, peak)
+        extras["d2_law"] = d2_law_check()
         extras["error_vs_fp64"] = accuracy_check()
         if not args.no_serve:
             extras["batched"] = batched_check(args.serve_instances, 200, peak)

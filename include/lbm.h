@@ -60,7 +60,10 @@ typedef enum { LBM_T_PERIODIC = 0, LBM_T_DIRICHLET = 1, LBM_T_ADIABATIC = 2 } lb
  *            LBM_OPEN (zero-gradient extrapolation of the unknown populations).
  *  therm[e]: LBM_T_PERIODIC, LBM_T_DIRICHLET (halfway anti-bounce-back to
  *            T_edge[e]) or LBM_T_ADIABATIC (halfway bounce-back).
- *  An axis is periodic for both lattices on both of its edges or not at all.
+ *  Each lattice is periodic along an axis on both of its edges or on neither.
+ *  A periodic thermal axis needs a periodic flow axis; a periodic flow axis
+ *  may carry Dirichlet or adiabatic thermal edges (Section 4.1: the droplet
+ *  in open space streams f periodically and holds T = T_g at the edges).
  *  theta_deg: equilibrium contact angle of walls (Section 3.3).
  *  heater_x0..heater_x1-1: south-edge nodes held at T_heater instead of
  *  T_edge[S] (Section 4.3). */

@@ -321,11 +321,16 @@ static int valid_bc(int nx, int ny, const orc_bc* bc) {
     for (int e = 0; e < 4; ++e) {
         if (bc->flow[e] < 0 || bc->flow[e] > 2) return 0;
         if (bc->therm[e] < 0 || bc->therm[e] > 2) return 0;
-        /* periodicity is a property of an axis, shared by both lattices */
-        if ((bc->flow[e] == ORC_PERIODIC) != (bc->therm[e] == ORC_T_PERIODIC)) return 0;
+        /* a periodic thermal edge needs a periodic flow edge; a periodic flow
+         * edge may carry a Dirichlet or adiabatic thermal edge: Section 4.1
+         * streams the flow populations periodically and holds T = T_g at the
+         * edges by halfway anti-bounce-back */
+        if (bc->therm[e] == ORC_T_PERIODIC && bc->flow[e] != ORC_PERIODIC) return 0;
     }
     if ((bc->flow[ORC_W] == ORC_PERIODIC) != (bc->flow[ORC_E] == ORC_PERIODIC)) return 0;
     if ((bc->flow[ORC_S] == ORC_PERIODIC) != (bc->flow[ORC_N] == ORC_PERIODIC)) return 0;
+    if ((bc->therm[ORC_W] == ORC_T_PERIODIC) != (bc->therm[ORC_E] == ORC_T_PERIODIC)) return 0;
+    if ((bc->therm[ORC_S] == ORC_T_PERIODIC) != (bc->therm[ORC_N] == ORC_T_PERIODIC)) return 0;
     /* walls are horizontal (south / north) only */
     if (bc->flow[ORC_W] == ORC_WALL || bc->flow[ORC_E] == ORC_WALL) return 0;
     if (bc->flow[ORC_W] != ORC_PERIODIC && nx < 2) return 0;

@@ -45,10 +45,16 @@ Layout layout_for(int nx, int ny, int prec) {
 bool bc_valid(int nx, int ny, const lbm_bc* bc) {
     for (int e = 0; e < 4; ++e) {
         if (bc->flow[e] < 0 || bc->flow[e] > 2 || bc->therm[e] < 0 || bc->therm[e] > 2) return false;
-        if ((bc->flow[e] == LBM_PERIODIC) != (bc->therm[e] == LBM_T_PERIODIC)) return false;
+        // a periodic thermal edge needs a periodic flow edge; a periodic flow
+        // edge may carry a Dirichlet or adiabatic thermal edge (Section 4.1)
+        if (bc->therm[e] == LBM_T_PERIODIC && bc->flow[e] != LBM_PERIODIC) return false;
     }
     if ((bc->flow[LBM_EDGE_W] == LBM_PERIODIC) != (bc->flow[LBM_EDGE_E] == LBM_PERIODIC)) return false;
     if ((bc->flow[LBM_EDGE_S] == LBM_PERIODIC) != (bc->flow[LBM_EDGE_N] == LBM_PERIODIC)) return false;
+    if ((bc->therm[LBM_EDGE_W] == LBM_T_PERIODIC) != (bc->therm[LBM_EDGE_E] == LBM_T_PERIODIC))
+        return false;
+    if ((bc->therm[LBM_EDGE_S] == LBM_T_PERIODIC) != (bc->therm[LBM_EDGE_N] == LBM_T_PERIODIC))
+        return false;
     if (bc->flow[LBM_EDGE_W] == LBM_WALL || bc->flow[LBM_EDGE_E] == LBM_WALL) return false;
     if (bc->flow[LBM_EDGE_W] != LBM_PERIODIC && nx < 2) return false;
     if (bc->flow[LBM_EDGE_S] != LBM_PERIODIC && ny < 2) return false;

@@ -209,7 +209,7 @@ struct Sweep {
     SM& S;
     WallRings<R, NT>& WR;   // valid only for domains with walls
     int t, nx, ny, pitch, y0, y1;
-    bool perx, pery, first, use_mass, wallS, wallN;
+    bool perx, pery, tperx, tpery, first, use_mass, wallS, wallN;
     unsigned plane;
     const TF* __restrict__ fsrc;
     const TG* __restrict__ gsrc;
@@ -249,6 +249,10 @@ struct Sweep {
         const int x0 = U.x0, x1 = U.x1;
         perx = I.flow[EW] == PERIODIC;
         pery = I.flow[ES] == PERIODIC;
+        // the thermal lattice may have Dirichlet / adiabatic edges on an axis
+        // along which the flow is periodic (Section 4.1)
+        tperx = I.therm[EW] == T_PERIODIC;
+        tpery = I.therm[ES] == T_PERIODIC;
         const long long step = __ldcg(&I.ctl->step);
         const int par = (int)(step & 1);
         first = step == 0;
@@ -287,8 +291,8 @@ struct Sweep {
         inB = colvalid && X >= x0 - 2 && X < x1 + 2;
         inC = colvalid && X >= x0 - 1 && X < x1 + 1;
         inD = X >= x0 && X < x1;
-        left_edge = !perx && X == 0;
-        right_edge = !perx && X == nx - 1;
+        left_edge = !tperx && X == 0;
+        right_edge = !tperx && X == nx - 1;
 
         // thermal boundary values, as deviations from T_ref (halfway
         // anti-bounce-back A = -g*_opp + 2 w^ (T_w - T_ref) in deviation form)
@@ -298,11 +302,11 @@ struct Sweep {
         dirN = I.therm[EN] == T_DIRICHLET;
         R twW = R(0), twE = R(0), twS = R(0), twN = R(0);
         TgS_l = TgS_c = TgS_r = TgN = R(0);
-        if (!perx) {
+        if (!tperx) {
             twW = (R)(I.T_edge[EW] - I.T_ref);
             twE = (R)(I.T_edge[EE] - I.T_ref);
         }
-        if (!pery && inD) {
+        if (!tpery && inD) {
             twS = (R)(wall_T(I, ES, gx) - I.T_ref);
             twN = (R)(I.T_edge[EN] - I.T_ref);
         }
@@ -852,7 +856,7 @@ struct Sweep {
                 if (P.frozen_thermal) {
                     go[0] = o0.x; go[1] = o0.y; go[2] = o0.z; go[3] = o0.w; go[4] = o1.x;
                 } else {
-                    const bool vd = STEADY || pery || r - 1 >= 0, vu = STEADY || pery || r + 1 < ny;
+                    const bool vd = STEADY || tpery || r - 1 >= 0, vu = STEADY || tpery || r + 1 < ny;
                     // gs planes hold g*_1, g*_2, g*_3; g*_0 and g*_4 of row r sit
                     // in the row's own slot, g*_4 of row r + 1 in that row's
                     const R* gsc = &S.gs[a1][0][t];
@@ -927,7 +931,7 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
     // iterations whose five stages are all active on rows with interior
     // neighbours take the steady form
     int klo = y0 + 4, khi = y1 + 2;
-    if (!w.pery) {
+    if (!w.pery || !w.tpery) {
         klo = max(klo, 5);
         khi = min(khi, I.ny - 2);
     }

@@ -151,6 +151,23 @@ def open_evaporation(nx=256, ny=256, R=40.0, w=4.0, T_sat=0.86, T_edge=0.95, amp
                 rho, z, z.copy(), T, steps, rl, rg)
 
 
+def d2_droplet(n=200, D0=60.0, w=4.0, T_sat=0.86, T_g=1.0, amp=0.0, seed=2, steps=20000,
+               p=None) -> Case:
+    """The D^2-law test of Section 4.1 as the paper states it: an n x n box,
+    a centred droplet of diameter D0 at T_sat in vapour at T_g, the flow
+    populations streamed periodically at the edges and T = T_g held on all
+    four edges (halfway anti-bounce-back)."""
+    rg, rl = COEXISTENCE[T_sat]
+    c0 = 0.5 * (n - 1)
+    rho = tanh_disc(n, n, c0, c0, 0.5 * D0, w, rl, rg)
+    if amp:
+        rho = rho + noise(seed, (n, n), amp)
+    T = tanh_disc(n, n, c0, c0, 0.5 * D0, w, T_sat * TC, T_g * TC)
+    z = np.zeros((n, n))
+    bc = bc_spec([PERIODIC] * 4, [T_DIRICHLET] * 4, T_edge=[T_g * TC] * 4)
+    return Case("d2_droplet_%d" % n, n, n, p or params(), bc, rho, z, z.copy(), T, steps, rl, rg)
+
+
 def heated_surface(nx=400, ny=200, R=50.0, w=5.0, T_sat=0.86, T_wall=0.95, theta=90.0,
                    amp=0.0, seed=3, steps=30000, p=None) -> Case:
     """Sessile droplet on a heated wall (Section 4.2 shape): wall at the

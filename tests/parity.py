@@ -76,6 +76,10 @@ def bc_variants():
         "open_x_periodic_y": W.bc_spec([W.OPEN, W.OPEN, W.PERIODIC, W.PERIODIC],
                                        [W.T_DIRICHLET, W.T_ADIABATIC, W.T_PERIODIC,
                                         W.T_PERIODIC], T_edge=[T2, 0, 0, 0]),
+        # Section 4.1: periodic flow, temperature held at the edges
+        "periodic_flow_fixed_T": W.bc_spec([W.PERIODIC] * 4,
+                                           [W.T_DIRICHLET, W.T_ADIABATIC, W.T_DIRICHLET,
+                                            W.T_DIRICHLET], T_edge=[T2, 0, T1, 1.0 * Tc]),
     }
 
 

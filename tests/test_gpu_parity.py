@@ -53,7 +53,8 @@ def test_tiny_domains_every_boundary_fp64(name, size):
     assert max(pe.values()) <= 1e-12, (name, pe)
 
 
-@pytest.mark.parametrize("name", ["periodic", "wall_open_heater", "open_x_walls_y"])
+@pytest.mark.parametrize("name", ["periodic", "wall_open_heater", "open_x_walls_y",
+                                  "periodic_flow_fixed_T"])
 @pytest.mark.parametrize("tile", [(128, 16), (256, 7), (128, 75)])
 def test_ragged_multi_tile_fp64(name, tile):
     """250 x 75 spans several strips and segments with ragged tails."""
@@ -78,6 +79,7 @@ def test_ragged_multi_tile_reduced_precision(prec, tol, name, tile):
     (lambda: W.open_evaporation(256, 256, steps=0), 200),
     (lambda: W.heated_surface(400, 200, steps=0), 100),
     (lambda: W.nucleate_boiling(300, 600, gravity=2e-5, steps=0), 60),
+    (lambda: W.d2_droplet(200, steps=0), 200),
 ])
 def test_workload_shapes_fp64(case_fn, steps):
     c = case_fn()
@@ -123,7 +125,7 @@ def test_tiles_give_identical_results():
 @pytest.mark.parametrize("prec", ["fp32", "fp32_g16"])
 @pytest.mark.parametrize("name", ["periodic", "open_dirichlet", "wall_open_heater",
                                   "two_walls_adiabatic", "open_x_walls_y", "periodic_x_open_y",
-                                  "open_x_periodic_y"])
+                                  "open_x_periodic_y", "periodic_flow_fixed_T"])
 @pytest.mark.parametrize("size", [(36, 20), (64, 48), (250, 75), (200, 40), (17, 13)])
 def test_staged_rows_equal_register_rows(name, size, prec):
     """The step with its rows staged in shared memory by bulk copies does the

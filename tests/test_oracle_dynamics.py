@@ -326,3 +326,40 @@ def test_literal_cv_reading_is_unstable():
     s = run_case(c)
     rc = s.step(400, check=False)
     assert rc in (-3, -4)      # non-finite fields or a negative psi^2
+
+
+def test_periodic_flow_with_dirichlet_temperature_edges():
+    """Section 4.1 streams the flow populations periodically and holds T = T_g
+    on the edges by halfway anti-bounce-back.  (a) Mass is conserved to
+    round-off (periodic flow) while the thermal edges exchange heat;
+    (b) with the flow frozen the thermal lattice sees only the two Dirichlet
+    edges, so the transient equals the one between flow walls bit for bit,
+    and its steady state is exactly linear across a two-phase rho c_v."""
+    c = W.d2_droplet(40, D0=16.0, T_g=0.95)
+    s = run_case(c)
+    d0 = s.diagnostics(c.rho_l, c.rho_g)
+    s.step(300)
+    d1 = s.diagnostics(c.rho_l, c.rho_g)
+    assert abs(d1["mass"] - d0["mass"]) <= 1e-12 * d0["mass"]
+    ny, T1, T2 = 16, 0.08, 0.11
+    rho = np.where(np.arange(ny)[:, None] < ny // 2, 0.5, 3.0) * np.ones((1, 4))
+    z = np.zeros((ny, 4))
+    th = [W.T_PERIODIC, W.T_PERIODIC, W.T_DIRICHLET, W.T_DIRICHLET]
+    out = {}
+    for name, fl in (("periodic", [W.PERIODIC] * 4),
+                     ("walls", [W.PERIODIC, W.PERIODIC, W.WALL, W.WALL])):
+        sm = O.Sim(4, ny, W.params(frozen_flow=1, cv=2.0), W.bc_spec(fl, th, T_edge=[0, 0, T1, T2]))
+        sm.init(rho, z, z, np.full((ny, 4), 0.5 * (T1 + T2)))
+        sm.step(300)
+        out[name] = sm.fields()[3].copy()
+        sm.step(40000)
+        out[name + "_steady"] = sm.fields()[3][:, 0].copy()
+    assert np.array_equal(out["periodic"], out["walls"])
+    exact = T1 + (T2 - T1) * (np.arange(ny) + 0.5) / ny
+    assert np.abs(out["periodic_steady"] - exact).max() < 1e-11
+
+
+def test_thermal_periodic_without_flow_periodic_is_refused():
+    spec = W.bc_spec([W.OPEN] * 4, [W.T_PERIODIC] * 4)
+    with pytest.raises(Exception):
+        O.Sim(8, 8, W.params(), spec)
