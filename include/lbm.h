@@ -321,6 +321,16 @@ int lbm_autotune(lbm_ctx* ctx, int steps_per_trial);
 int lbm_set_staging(lbm_ctx* ctx, int on);
 int lbm_get_staging(const lbm_ctx* ctx);
 
+/* Test hook for the staged path's failure detection (no counterpart in the
+ * paper).  on = 1: every CTA of the context's next staged launches also waits
+ * on an mbarrier that nothing ever arms; that wait is bounded like the row
+ * waits (about 2^31 clocks, roughly a second), runs out, and the launch
+ * records LBM_ETIMEOUT in the sticky error word.  The row pipeline keeps its
+ * own waits, so the step's results are unchanged and no copy is left in
+ * flight; the GPU is never faulted.  No effect on the register-prefetch path
+ * or on batches.  Returns LBM_EINVAL for NULL, LBM_ESTATE in a batch. */
+int lbm_set_wait_probe(lbm_ctx* ctx, int on);
+
 /* ---- diagnostics without any allocation -------------------------------- *
  * The paper has no counterpart to this call; it exists for callers that may
  * not allocate device memory: a process whose GPU memory is owned by another

@@ -39,7 +39,8 @@ ABI_FUNCTIONS = (
     "lbm_batch_create", "lbm_batch_attach", "lbm_batch_detach", "lbm_batch_size",
     "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy", "lbm_batch_autotune",
     "lbm_batch_get_tile", "lbm_set_tile", "lbm_get_tile",
-    "lbm_autotune", "lbm_set_staging", "lbm_get_staging", "lbm_diag_reduce_noalloc", "lbm_reconfigure", "lbm_contact_angle",
+    "lbm_autotune", "lbm_set_staging", "lbm_get_staging", "lbm_set_wait_probe",
+    "lbm_diag_reduce_noalloc", "lbm_reconfigure", "lbm_contact_angle",
     "lbm_regions",
     # include/lbm3d.h
     "lbm3d_state_bytes", "lbm3d_create", "lbm3d_init_fields", "lbm3d_step", "lbm3d_get_fields",
@@ -142,6 +143,7 @@ def lib():
             "lbm_autotune": ([_vp, ctypes.c_int], ctypes.c_int),
             "lbm_set_staging": ([_vp, ctypes.c_int], ctypes.c_int),
             "lbm_get_staging": ([_vp], ctypes.c_int),
+            "lbm_set_wait_probe": ([_vp, ctypes.c_int], ctypes.c_int),
             "lbm_diag_reduce_noalloc": ([_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, _vp, _vp],
                                         ctypes.c_int),
@@ -321,6 +323,11 @@ class Domain:
     @staged.setter
     def staged(self, on: bool):
         _check(lib().lbm_set_staging(self._h, 1 if on else 0), self._h)
+
+    def set_wait_probe(self, on: bool):
+        """Test hook: staged launches also wait on an mbarrier nothing arms,
+        so each CTA's bounded wait runs out and LBM_ETIMEOUT is reported."""
+        _check(lib().lbm_set_wait_probe(self._h, 1 if on else 0), self._h)
 
     @property
     def last_error(self) -> str:

@@ -212,7 +212,7 @@ struct lbm_ctx {
     Inst* inst_dev = nullptr;
     unsigned* sched = nullptr;
     Unit* units = nullptr;
-    int n_units = 0, grid = 1, threads = 128, rows = 64, staged = 0;
+    int n_units = 0, grid = 1, threads = 128, rows = 64, staged = 0, wait_probe = 0;
     cudaGraphExec_t graph = nullptr;
     long long step = 0;
     bool initialized = false;
@@ -259,9 +259,10 @@ static int cuda_err(lbm_ctx* c, cudaError_t e, const char* where) {
 }
 
 static int map_device_err(int bits) {
+    // a wait that ran out comes first: it can be the cause of the others
+    if (bits & ERR_TIMEOUT) return LBM_ETIMEOUT;
     if (bits & ERR_PSI) return LBM_EPSI;
     if (bits & ERR_NONFINITE) return LBM_ENONFINITE;
-    if (bits & ERR_TIMEOUT) return LBM_ETIMEOUT;
     return LBM_OK;
 }
 
@@ -307,6 +308,7 @@ static StepLaunch ctx_launch(const lbm_ctx* c) {
     L.grid = c->grid;
     L.walls = has_walls(c->inst) ? 1 : 0;
     L.staged = c->staged;
+    L.wait_probe = c->wait_probe;
     L.phys = c->phys;
     return L;
 }
@@ -351,8 +353,9 @@ static int ctx_check(lbm_ctx* c) {
     if (rc) return rc;
     if (h.err && c->sticky == LBM_OK) {
         c->sticky = map_device_err(h.err);
-        c->err = c->sticky == LBM_EPSI ? "psi^2 < 0 at some node (density above the EOS range)"
-                                       : "non-finite density or temperature";
+        c->err = c->sticky == LBM_ETIMEOUT ? "a bounded wait for a staged row ran out"
+                 : c->sticky == LBM_EPSI ? "psi^2 < 0 at some node (density above the EOS range)"
+                                         : "non-finite density or temperature";
     }
     return c->sticky;
 }
@@ -982,6 +985,14 @@ int lbm_set_staging(lbm_ctx* c, int on) {
 
 int lbm_get_staging(const lbm_ctx* c) { return c ? c->staged : LBM_EINVAL; }
 
+int lbm_set_wait_probe(lbm_ctx* c, int on) {
+    if (!c) return LBM_EINVAL;
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    c->wait_probe = on ? 1 : 0;
+    drop_graph(&c->graph);
+    return LBM_OK;
+}
+
 int lbm_get_tile(const lbm_ctx* c, int* threads, int* rows) {
     if (!c) return LBM_EINVAL;
     if (threads) *threads = c->threads;
@@ -1175,6 +1186,7 @@ int lbm_batch_step(lbm_batch* b, int n) {
     L.grid = b->grid;
     L.walls = b->walls;
     L.staged = b->staged;
+    L.wait_probe = 0;
     L.phys = b->phys;
     int rc = enqueue_steps(b->stream, &b->graph, L, b->prec, b->threads, n, b->members[0]);
     if (rc == LBM_OK)

@@ -114,6 +114,7 @@ struct StageSmem {
     R gs[3][3][NT];
     typename Vec2<R>::T own[5][NT];   // rho, then T (dp/dT)_rho -> g*_0 after stage C
     unsigned long long mbar[D + 1];
+    unsigned long long probe;   // never armed: the wait-timeout test hook waits on it
     double red[NT / 32];
     int unit;
 };
@@ -159,16 +160,19 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* m, unsigned parity
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// bounded wait for a staged row: gives up after ~2^31 clocks (about a
-// second) and reports it; a thread that gave up stops waiting for the rest of
-// the launch (its results are then invalid and the sticky error says so)
-__device__ __forceinline__ void wait_row(unsigned long long* m, unsigned parity, int* err) {
-    if (*err & ERR_TIMEOUT) return;
+// bounded wait for an mbarrier phase: gives up after ~2^31 clocks (about a
+// second at the GB300's clock), records ERR_TIMEOUT and sets *stalled; a
+// thread that has stalled does not wait again on the same pipeline (its
+// results are then invalid and the sticky error says so)
+__device__ __forceinline__ void wait_row(unsigned long long* m, unsigned parity, int* err,
+                                         bool* stalled) {
+    if (*stalled) return;
     if (mbar_test(m, parity)) return;
     const long long t0 = clock64();
     while (!mbar_test(m, parity)) {
         if (clock64() - t0 > (1LL << 31)) {
             *err |= ERR_TIMEOUT;
+            *stalled = true;
             return;
         }
     }
@@ -236,6 +240,7 @@ struct Sweep {
     // one unit to the next)
     int X0w, sidx, gq, fq, kw2, scs, X0g, goff, gcs;
     unsigned mph, sbytes, gbytes, rbytes;
+    bool stalled;   // a staged-row wait ran out in this unit
 
     __device__ __forceinline__ Sweep(const Inst& I_, const Unit& U, const Phys<R>& P_, SM& S_,
                                      WallRings<R, NT>& WR_, int fq0, unsigned mph0)
@@ -345,6 +350,7 @@ struct Sweep {
         gq = 0;
         fq = fq0;
         mph = mph0;
+        stalled = false;
         if constexpr (STG) {
             // copy extent of one plane row: open x copies the columns inside
             // the domain, periodic x the whole window
@@ -619,7 +625,7 @@ struct Sweep {
 
         // ---- A(k): moments, EOS, psi
         if constexpr (STG) {
-            wait_row(&S.mbar[fq], (mph >> fq) & 1u, &errbits);
+            wait_row(&S.mbar[fq], (mph >> fq) & 1u, &errbits, &stalled);
             mph ^= 1u << fq;
         }
         R rho_a = R(1), rhod_a = R(0), jx_a = R(0), jy_a = R(0), psi_a = R(0), ir_a = R(1);
@@ -925,9 +931,18 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
                                              const Phys<typename Types<PREC>::R>& P,
                                              typename Sweep<PREC, NT, UNIT, STG>::SM& S,
                                              WallRings<typename Types<PREC>::R, NT>& WR,
-                                             int& fq, unsigned& mph) {
+                                             int& fq, unsigned& mph, int probe) {
     Sweep<PREC, NT, UNIT, STG> w(I, U, P, S, WR, fq, mph);
     const int y0 = U.y0, y1 = U.y1;
+    if constexpr (STG) {
+        // wait-timeout test hook: a bounded wait on an mbarrier that nothing
+        // arms runs out and records ERR_TIMEOUT; the row pipeline keeps its
+        // own waits, so the step itself is unaffected
+        if (probe) {
+            bool probe_stalled = false;
+            wait_row(&S.probe, 0u, &w.errbits, &probe_stalled);
+        }
+    }
     // iterations whose five stages are all active on rows with interior
     // neighbours take the steady form
     int klo = y0 + 4, khi = y1 + 2;
@@ -948,6 +963,17 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
     for (; k <= y1 + 3; ++k) w.iter_general(k);
     fq = w.fq;
     mph = w.mph;
+    if constexpr (STG) {
+        // a row wait that ran out may leave copies in flight into this CTA's
+        // shared memory: wait (again bounded) until each row mbarrier has
+        // completed the last phase this unit used, before the CTA moves on
+        if (w.stalled) {
+            for (int m = 0; m < Sweep<PREC, NT, UNIT, STG>::NF; ++m) {
+                bool st = false;
+                wait_row(&S.mbar[m], ((mph >> m) & 1u) ^ 1u, &w.errbits, &st);
+            }
+        }
+    }
 
     if (w.errbits) atomicOr(&I.ctl->err, w.errbits);
     if (w.use_mass) {
@@ -980,6 +1006,7 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
     if constexpr (STG) {
         if (threadIdx.x == 0) {
             for (int m = 0; m <= Ahead<NT>::value; ++m) mbar_init(&S.mbar[m], 1);
+            mbar_init(&S.probe, 1);
             mbar_init_fence();
         }
         __syncthreads();
@@ -991,7 +1018,7 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
         __syncthreads();
         if (u >= L.n_units) break;
         const Unit U = L.units[u];
-        process_unit<PREC, NT, UNIT, STG>(L.insts[U.inst], U, P, S, WR, fq, mph);
+        process_unit<PREC, NT, UNIT, STG>(L.insts[U.inst], U, P, S, WR, fq, mph, L.wait_probe);
     }
     if (threadIdx.x == 0) {
         __threadfence();

@@ -291,3 +291,40 @@ def test_full_size_mass_conserved_fp32():
     d.step(500)
     m1 = d.diagnostics(c.rho_l, c.rho_g)["mass"]
     assert abs(m1 - m0) <= 1e-5 * m0
+
+
+def test_staged_wait_timeout_is_reported_not_hung():
+    """Failure detection of the staged path without a GPU fault: with the test
+    hook on, every CTA also waits on an mbarrier that nothing arms.  The wait
+    is bounded (about a second), the launch ends, LBM_ETIMEOUT is reported
+    through the sticky error word, the step's populations equal a normal
+    step's (the row pipeline kept its own waits), and after lbm_init_fields
+    the context steps normally again."""
+    import time
+
+    import paper_2205_00686_gb300 as lbm
+    c = W.static_droplet()
+    ref = P.run_gpu(c, 1, "fp32", staged=True)
+    d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+    d.staged = True
+    d.init_fields(*c.fields())
+    d.set_wait_probe(True)
+    t0 = time.perf_counter()
+    d.step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        d.sync()
+    assert e.value.code == lbm.LBM_ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    # the readback still copies the state, then reports the sticky error
+    f = np.empty((9, c.ny, c.nx))
+    g = np.empty((5, c.ny, c.nx))
+    Pp = np.empty((c.ny, c.nx))
+    rc = lbm.lib().lbm_get_populations(d.handle, *[lbm._ptr(a) for a in (f, g, Pp)])
+    assert rc == lbm.LBM_ETIMEOUT
+    for a, b in zip((f, g, Pp), ref.populations()):
+        assert np.array_equal(a, b)
+    d.set_wait_probe(False)
+    d.init_fields(*c.fields())
+    d.step(5)
+    d.sync()
+    assert d.step_count == 5
