@@ -159,3 +159,17 @@ def test_invariants_at_256_cubed():
         for u in (ux, uy, uz):
             assert abs((rho * u).sum()) <= 1e-4 * np.abs(rho * u).sum(), c.name
         d.close()
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_multi_block_domain_matches_oracle(walls):
+    """A domain of several 32 x 4 thread blocks with ragged x and y edges
+    (45 x 9) and 70 planes, periodic z and between walls, against the oracle
+    in FP64 after 30 steps."""
+    Tc = W.TC
+    c = with_T_bump(W.droplet3d(45, 9, 70, R=6.0, amp=1e-3, p=W.params(gravity=2e-5)))
+    if walls:
+        c.bc = W.wall_bc3(0.95 * Tc, 0.88 * Tc, theta_deg=70.0)
+    d, o = run_both(c, 30, "fp64")
+    e = fields_err(d, o)
+    assert max(e.values()) <= 1e-10, e
