@@ -348,7 +348,10 @@ struct Sweep {
         X0w = x0 - 4;
         sidx = perx ? t : gxl - X0w;
         gq = 0;
-        fq = fq0;
+        // the f ring restarts with each unit (every row of the previous unit
+        // was waited for); the mbarriers' next phase parities carry over
+        fq = 0;
+        (void)fq0;
         mph = mph0;
         stalled = false;
         if constexpr (STG) {
@@ -477,7 +480,7 @@ struct Sweep {
         if constexpr (STG) {
             if (k + DA <= y1 + 3)
                 issue_row(k + DA, kw2, gq + DA >= NGS ? gq + DA - NGS : gq + DA,
-                          fq == 0 ? NF - 1 : fq - 1);
+                          NF == 3 ? a1 : (fq == 0 ? NF - 1 : fq - 1));
         }
         // ================= phase alpha =================
         const bool doA = STEADY || (k < y1 + 3 && rowvalid(k));
@@ -625,13 +628,16 @@ struct Sweep {
 
         // ---- A(k): moments, EOS, psi
         if constexpr (STG) {
-            wait_row(&S.mbar[fq], (mph >> fq) & 1u, &errbits, &stalled);
-            mph ^= 1u << fq;
+            // with three f slots the f ring turns with the literal ring slots:
+            // row k sits in slot a0
+            const int fk = NF == 3 ? a0 : fq;
+            wait_row(&S.mbar[fk], (mph >> fk) & 1u, &errbits, &stalled);
+            mph ^= 1u << fk;
         }
         R rho_a = R(1), rhod_a = R(0), jx_a = R(0), jy_a = R(0), psi_a = R(0), ir_a = R(1);
         if constexpr (STG) {
             if (doA && (STEADY || colvalid)) {
-                const R* fr = &S.fR[fq][0][sidx];
+                const R* fr = &S.fR[NF == 3 ? a0 : fq][0][sidx];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) fa[q] = fr[q * NT];
                 const TG* gr = &S.gR[gq][0][sidx + goff];
@@ -690,7 +696,7 @@ struct Sweep {
         // staged form: every thread is past its wait for row k, so row k's
         // mbarrier (and f slot) can take row k + 3
         if constexpr (STG) {
-            if (k + DA + 1 <= y1 + 3) arm_row(k + DA + 1, fq);
+            if (k + DA + 1 <= y1 + 3) arm_row(k + DA + 1, NF == 3 ? a0 : fq);
         }
 
         // ---- B(k-1): interaction force, velocity, D2Q9 MRT collision
