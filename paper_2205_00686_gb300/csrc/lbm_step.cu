@@ -234,16 +234,15 @@ struct Sweep {
     int errbits;
     int ra0, ra1, ra2, b0, kw;
     // staged form: window start column, this column's index in a staged row,
-    // slot of row k in the g/P ring (of 7), slot and mbarrier of row k in the
-    // f ring (of 3), and the phase parity each f mbarrier completes next
-    // (bit m for mbarrier m; the f ring and the mbarriers carry over from
-    // one unit to the next)
+    // slot of row k in the g/P ring, slot and mbarrier of row k in the f ring
+    // (both restart with each unit), and the phase parity each f mbarrier
+    // completes next (bit m for mbarrier m; carried over from unit to unit)
     int X0w, sidx, gq, fq, kw2, scs, X0g, goff, gcs;
     unsigned mph, sbytes, gbytes, rbytes;
     bool stalled;   // a staged-row wait ran out in this unit
 
     __device__ __forceinline__ Sweep(const Inst& I_, const Unit& U, const Phys<R>& P_, SM& S_,
-                                     WallRings<R, NT>& WR_, int fq0, unsigned mph0)
+                                     WallRings<R, NT>& WR_, unsigned mph0)
         : I(I_), P(P_), S(S_), WR(WR_) {
         t = threadIdx.x;
         nx = I.nx;
@@ -351,7 +350,6 @@ struct Sweep {
         // the f ring restarts with each unit (every row of the previous unit
         // was waited for); the mbarriers' next phase parities carry over
         fq = 0;
-        (void)fq0;
         mph = mph0;
         stalled = false;
         if constexpr (STG) {
@@ -937,8 +935,8 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
                                              const Phys<typename Types<PREC>::R>& P,
                                              typename Sweep<PREC, NT, UNIT, STG>::SM& S,
                                              WallRings<typename Types<PREC>::R, NT>& WR,
-                                             int& fq, unsigned& mph, int probe) {
-    Sweep<PREC, NT, UNIT, STG> w(I, U, P, S, WR, fq, mph);
+                                             unsigned& mph, int probe) {
+    Sweep<PREC, NT, UNIT, STG> w(I, U, P, S, WR, mph);
     const int y0 = U.y0, y1 = U.y1;
     if constexpr (STG) {
         // wait-timeout test hook: a bounded wait on an mbarrier that nothing
@@ -967,7 +965,6 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
         w.template iter<true>(k + 2, 2, 1, 0);
     }
     for (; k <= y1 + 3; ++k) w.iter_general(k);
-    fq = w.fq;
     mph = w.mph;
     if constexpr (STG) {
         // a row wait that ran out may leave copies in flight into this CTA's
@@ -1007,7 +1004,6 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM& S = *reinterpret_cast<SM*>(smem_raw);
     WallRings<R, NT>& WR = *reinterpret_cast<WallRings<R, NT>*>(smem_raw + sizeof(SM));
-    int fq = 0;
     unsigned mph = 0;
     if constexpr (STG) {
         if (threadIdx.x == 0) {
@@ -1024,7 +1020,7 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
         __syncthreads();
         if (u >= L.n_units) break;
         const Unit U = L.units[u];
-        process_unit<PREC, NT, UNIT, STG>(L.insts[U.inst], U, P, S, WR, fq, mph, L.wait_probe);
+        process_unit<PREC, NT, UNIT, STG>(L.insts[U.inst], U, P, S, WR, mph, L.wait_probe);
     }
     if (threadIdx.x == 0) {
         __threadfence();
