@@ -1099,8 +1099,12 @@ static int batch_rebuild(lbm_batch* b) {
     for (size_t i = 0; i < b->members.size(); ++i) {
         build_units(b->members[i]->inst, (int)i, b->threads, std::min(b->rows, b->members[i]->ny), us);
     }
-    // longest-first is not needed: units of one batch are near-equal in size;
-    // keep domain order so neighbouring units share halos in L2
+    // longest first: a unit's sweep takes (rows + 6) iterations whatever its
+    // width, and the persistent CTAs take units in list order, so the tall
+    // units go first and the short ones fill the tail; units of equal height
+    // keep domain order, so neighbouring units share halos in L2
+    std::stable_sort(us.begin(), us.end(),
+                     [](const Unit& a, const Unit& b) { return a.y1 - a.y0 > b.y1 - b.y0; });
     cudaError_t e = cudaMalloc(&b->insts, hi.size() * sizeof(Inst));
     if (e == cudaSuccess) e = cudaMalloc(&b->units, us.size() * sizeof(Unit));
     if (e == cudaSuccess) e = cudaMemcpy(b->insts, hi.data(), hi.size() * sizeof(Inst), cudaMemcpyHostToDevice);
