@@ -328,3 +328,25 @@ def test_staged_wait_timeout_is_reported_not_hung():
     d.step(5)
     d.sync()
     assert d.step_count == 5
+
+
+def test_autotune_keeps_state_and_picks_a_valid_tile():
+    """lbm_autotune times load paths x threads x rows (powers of two and the
+    heights that fill the grid in whole waves) on a scratch domain: the
+    caller's state is untouched, the chosen tile is one of the candidates,
+    and a fresh domain of the same size starts with the cached choice."""
+    import paper_2205_00686_gb300 as lbm
+    c = P.droplet_case(600, 130, P.bc_variants()["open_dirichlet"])
+    d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+    d.init_fields(*c.fields())
+    d.step(7)
+    before = d.populations()
+    threads, rows = d.autotune(3)
+    assert threads in (128, 192, 224, 256) and 1 <= rows <= c.ny
+    for a, b in zip(d.populations(), before):
+        assert np.array_equal(a, b)
+    assert d.step_count == 7
+    e = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+    assert e.tile() == (threads, rows) and e.staged == d.staged
+    d.step(5)
+    d.sync()
