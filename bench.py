@@ -424,8 +424,12 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    if rank == 0 or world > 1:
+    # one process compiles (the objects and the library are in-tree, shared by
+    # every rank); the others wait for it before loading the library
+    if rank == 0:
         _build.build()
+    if world > 1:
+        dist.barrier()
     stream = torch.cuda.Stream()
     case = make_case(args.size, args.ny)
     N = case.nx * case.ny
