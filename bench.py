@@ -9,9 +9,15 @@ one coupled update of every node.  The state (2 x 1 GiB ping-pong buffers) is
 larger than L2, so no flush is needed between steps.
 
 Prints one JSON line: MLUPS (whole job), HBM roofline of the fused step
-kernel, the end-to-end figure through the C ABI with host buffers, clocks,
-the FP64 figure, each precision's error against the FP64 CPU oracle, and the
-oracle itself timed on the host cores as a baseline.
+kernel (against the measured copy bandwidth, and the nominal 8 TB/s), the
+end-to-end figure through the C ABI with host buffers, clocks, and the
+oracle itself timed on the host cores as a baseline.  Extras (rank 0): the
+FP64 step against the FP64 ALU roofline, the FP16-g variant, the 3-D form,
+the D^2 law of Section 4.1 (FP32 and FP64 evaporation constants) and the
+open-outflow configuration's d^2 slope, the FP32 / FP16-g field errors
+against the FP64 path (which matches the oracle to 1e-10 in the tests), the
+512-domain batch resident in one launch per step, and the same population
+served by the continuous-batching loop.
 
 Under torchrun (N > 1) every rank advances its own replica of the domain
 (the domains are independent: replicas, weak scaling) and rank 0 reports
