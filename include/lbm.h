@@ -294,9 +294,12 @@ int lbm_batch_get_tile(const lbm_batch* b, int* threads, int* rows, int* staged)
 
 /* ---- launch configuration ------------------------------------------------ *
  * Tile of the fused step: a strip of (threads - 8) columns swept over a
- * segment of `rows` rows.  threads is 128, 192, 224 or 256; rows >= 1.  The autotuner
- * times the candidates on a scratch domain of the same size and precision
- * and applies the fastest; its choice is cached per (precision, size). */
+ * segment of `rows` rows.  threads is 128, 192, 224 or 256; rows >= 1.
+ * Without tuning, lbm_create takes the height that makes the units fill the
+ * persistent grid in one wave.  The autotuner times load paths x thread
+ * counts x heights (powers of two and the whole-wave heights) on a scratch
+ * domain of the same size and precision, applies the fastest and caches the
+ * choice per (precision, size). */
 int lbm_set_tile(lbm_ctx* ctx, int threads, int rows);
 int lbm_get_tile(const lbm_ctx* ctx, int* threads, int* rows);
 int lbm_autotune(lbm_ctx* ctx, int steps_per_trial);
@@ -308,12 +311,12 @@ int lbm_autotune(lbm_ctx* ctx, int steps_per_trial);
  * use; on = 0: each thread loads its own column a half row ahead into
  * registers.  Both paths do the same arithmetic in the same order; results
  * agree to rounding (the two kernels are compiled separately, so multiply-
- * adds may be contracted differently).  Staging needs LBM_FP32 or LBM_FP32_G16 and either open x
- * edges or a periodic x axis with nx >= 32 a multiple of 4 (LBM_FP32) or 8
- * (LBM_FP32_G16); lbm_create turns it on (with a 224-thread tile) for
- * wall-free domains wide enough for 216-column strips, lbm_autotune times
- * both paths.  Returns LBM_EINVAL
- * when on = 1 is not possible, LBM_ESTATE for a context in a batch.  A
+ * adds may be contracted differently).  Staging needs LBM_FP32 or
+ * LBM_FP32_G16 and either open x edges or a periodic x axis with nx >= 32 a
+ * multiple of 4 (LBM_FP32) or 8 (LBM_FP32_G16); lbm_create turns it on
+ * (with a 224-thread tile) for wall-free domains wide enough for 216-column
+ * strips, lbm_autotune times both paths.  Returns LBM_EINVAL when on = 1 is
+ * not possible, LBM_ESTATE for a context in a batch.  A
  * staged launch that waits more than about a second for a row reports
  * LBM_ETIMEOUT (sticky) instead of hanging.  lbm_get_staging returns 0 or 1
  * (LBM_EINVAL for NULL).  A batch stages (224-thread tile) when every member
