@@ -61,3 +61,14 @@ def test_3d_state_bytes(built_lib):
     assert lbm.lbm3d_state_bytes(64, 48, 40, "fp32") == 75 * 64 * 48 * 40 * 4
     assert lbm.lbm3d_state_bytes(33, 2, 3, "fp64") == 75 * 64 * 2 * 3 * 8
     assert lbm.lbm3d_state_bytes(8, 8, 8, "fp32_g16") == 0
+
+
+def test_sizes_beyond_the_plane_limit_are_refused(built_lib):
+    """lbm_create refuses, before any device call, a domain whose nine f
+    planes would pass 2^31 elements (the kernels' 32-bit plane offsets):
+    15424^2 is the largest square accepted, 15488^2 is refused."""
+    import paper_2205_00686_gb300 as lbm
+    from paper_2205_00686_gb300 import workloads as W
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Domain(15488, 15488, W.params(), W.periodic_bc(), prec="fp32")
+    assert e.value.code == lbm.LBM_EINVAL

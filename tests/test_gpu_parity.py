@@ -350,3 +350,27 @@ def test_autotune_keeps_state_and_picks_a_valid_tile():
     assert e.tile() == (threads, rows) and e.staged == d.staged
     d.step(5)
     d.sync()
+
+
+def test_largest_accepted_domain_steps():
+    """The largest square FP32 domain lbm_create accepts (15424^2: the nine f
+    planes stay below 2^31 elements, 28 GB of state) steps in the default
+    staged launch: a uniform state is a fixed point of the step (every unit
+    of the persistent grid ran; nothing was read out of place), and the mass
+    is unchanged."""
+    import paper_2205_00686_gb300 as lbm
+    n = 15424
+    Tr = 0.86
+    rg, rl = W.COEXISTENCE[Tr]
+    d = lbm.Domain(n, n, W.params(), W.periodic_bc(), prec="fp32")
+    assert d.staged
+    rho = np.full((n, n), rg)
+    z = np.zeros((n, n))
+    d.init_fields(rho, z, z, np.full((n, n), Tr * W.TC))
+    del rho
+    m0 = d.diagnostics(rl, rg)["mass"]
+    d.step(3)
+    dg = d.diagnostics(rl, rg)
+    assert dg["nonfinite"] == 0 and dg["max_u"] < 1e-6
+    assert abs(dg["mass"] - m0) <= 1e-6 * m0
+    d.close()
