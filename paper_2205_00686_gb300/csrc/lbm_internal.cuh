@@ -139,7 +139,22 @@ __device__ __forceinline__ float f_rcp(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ double f_rcp(double x) { return 1.0 / x; }
+// FP64 reciprocal by the Newton-Raphson iteration for 1/x,
+// r <- r + r (1 - x r), which squares the relative error at each step: from
+// the hardware approximation rcp.approx.ftz.f64 two steps reach the FP64
+// rounding level (within about one ulp of 1/x, not always the correctly
+// rounded value).  The FP64 step divides six times per node and is bound by
+// the GB300's FP64 pipe.  Operands are O(1) here (rho, 1 - b rho, rho c_v,
+// sqrt(T/Tc)); a zero, infinite or NaN operand gives a non-finite result,
+// which the step reports.
+__device__ __forceinline__ double f_rcp(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
 __device__ __forceinline__ float f_sqrt(float x) {
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
