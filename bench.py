@@ -44,7 +44,7 @@ BYTES_PER_NODE = {"fp32": 120, "fp64": 240, "fp32_g16": 100}
 # FP64 FLOP per node update of the FP64 step (2 DFMA + DADD + DMUL thread
 # instructions per node, ncu on the same kernel: profiles/k_step_fp64_2048_alu.md)
 # and the nominal FP64 rate of the part (no measured FP64 peak on this machine)
-FP64_FLOP_PER_NODE = 368.0
+FP64_FLOP_PER_NODE = 344.7
 FP64_NOMINAL_GFLOPS = 1250.0
 METRIC = "coupled D2Q9+D2Q5 MLUPS and % of HBM roofline, FP32 vs FP64 at stated error"
 STEP_SOURCES = ["paper_2205_00686_gb300/csrc/lbm_step.cu",
