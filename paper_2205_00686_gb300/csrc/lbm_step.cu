@@ -239,6 +239,13 @@ struct Sweep {
     // completes next (bit m for mbarrier m; carried over from unit to unit)
     int X0w, sidx, gq, fq, kw2, scs, X0g, goff, gcs;
     unsigned mph, sbytes, gbytes, rbytes;
+    // this thread's part in the row copies, fixed for the unit: the plane it
+    // copies (-1: none; 0 f, 1 g, 2 P), the global address of that plane's
+    // row 0 at the first copied column, the shared-memory byte offset of the
+    // copy in slot 0, the bytes between slots, between rows and per copy
+    int cp_kind;
+    const char* cp_src;
+    unsigned cp_dst, cp_slot, cp_row, cp_bytes;
     bool stalled;   // a staged-row wait ran out in this unit
 
     __device__ __forceinline__ Sweep(const Inst& I_, const Unit& U, const Phys<R>& P_, SM& S_,
@@ -366,6 +373,32 @@ struct Sweep {
             const int gce = perx ? X0g + NTG : ((min(X0g + NTG, nx) + GA - 1) & ~(GA - 1));
             gbytes = (unsigned)((gce - gcs) * (int)sizeof(TG));
             rbytes = 10u * sbytes + 5u * gbytes;
+            // copy role: the 15 planes spread over the warps (plane = warp +
+            // nwarps * lane: 0..8 f, 9..13 g, 14 P), so that no warp carries
+            // the issue work alone
+            {
+                const int pl = (t >> 5) + (NT / 32) * (t & 31);
+                cp_kind = pl < 9 ? 0 : (pl < 14 ? 1 : (pl < 15 ? 2 : -1));
+                const bool isg = cp_kind == 1;
+                const int es = isg ? (int)sizeof(TG) : (int)sizeof(R);
+                const int w0 = isg ? X0g : X0w;
+                const int cs = isg ? gcs : scs;
+                const char* base = cp_kind == 0 ? (const char*)(fsrc + (size_t)pl * plane)
+                                   : isg        ? (const char*)(gsrc + (size_t)(pl - 9) * plane)
+                                                : (const char*)Psrc;
+                // periodic x copies the window in wrapped pieces from column 0
+                cp_src = base + (perx ? 0 : (size_t)cs * es);
+                const char* s0 = (const char*)&S;
+                const char* d0 = cp_kind == 0 ? (const char*)&S.fR[0][pl < 9 ? pl : 0][0]
+                                 : isg        ? (const char*)&S.gR[0][isg ? pl - 9 : 0][0]
+                                              : (const char*)&S.pR[0][0];
+                cp_dst = (unsigned)(d0 - s0) + (perx ? 0u : (unsigned)((cs - w0) * es));
+                cp_slot = cp_kind == 0 ? (unsigned)sizeof(S.fR[0])
+                          : isg        ? (unsigned)sizeof(S.gR[0])
+                                       : (unsigned)sizeof(S.pR[0]);
+                cp_row = (unsigned)(pitch * es);
+                cp_bytes = isg ? gbytes : sbytes;
+            }
             // iteration k queues the copies of row k + DA and arms row
             // k + DA + 1
             // rows y0 - 3 .. y0 - 3 + DA armed, the first DA of them
@@ -399,35 +432,22 @@ struct Sweep {
     __device__ __forceinline__ void arm_row(int k, int fslot) {
         if (t == 0) mbar_arrive_tx(&S.mbar[fslot], (k < y1 + 3 && rowvalid(k)) ? rbytes : 0u);
     }
-    // The bulk copies of row k (wrapped row kwr) into f slot fslot and g/P
-    // slot gslot.  The 15 planes are spread over the warps (plane = warp +
-    // nwarps * lane: 0..8 f, 9..13 g, 14 P) so that no warp carries the issue
-    // work alone.  Open x: the columns inside the domain (the last strip's
-    // copy rounded up to 4 columns, inside the row pitch); clamped columns
-    // read their edge column's entry (sidx).  Periodic x: the window in pieces
-    // that wrap around the axis.
+    // This thread's bulk copy (its plane from the copy role) of row k (wrapped
+    // row kwr) into f slot fslot or g/P slot gslot.  Open x: the columns
+    // inside the domain (the last strip's copy rounded up to 4 columns, inside
+    // the row pitch); clamped columns read their edge column's entry (sidx).
+    // Periodic x: the window in pieces that wrap around the axis.
     __device__ __forceinline__ void issue_row(int k, int kwr, int gslot, int fslot) {
-        if (!(k < y1 + 3 && rowvalid(k))) return;
-        constexpr int NW = NT / 32;
-        const int pl = (t >> 5) + NW * (t & 31);
-        if (pl >= 15) return;
+        if (cp_kind < 0 || !(k < y1 + 3 && rowvalid(k))) return;
         unsigned long long* mb = &S.mbar[fslot];
-        const size_t rowoff = (size_t)kwr * pitch;
-        // byte addresses of the plane row's column 0 in global and staged
-        // memory, the element size and the window of this plane
-        const bool isg = pl >= 9 && pl < 14;
-        const char* src = pl < 9 ? (const char*)(fsrc + (size_t)pl * plane + rowoff)
-                          : isg  ? (const char*)(gsrc + (size_t)(pl - 9) * plane + rowoff)
-                                 : (const char*)(Psrc + rowoff);
-        char* dst = pl < 9 ? (char*)&S.fR[fslot][pl][0]
-                    : isg  ? (char*)&S.gR[gslot][pl - 9][0]
-                           : (char*)&S.pR[gslot][0];
-        const int es = isg ? (int)sizeof(TG) : (int)sizeof(R);
-        const int w0 = isg ? X0g : X0w;
+        char* dst = (char*)&S + cp_dst + (unsigned)(cp_kind == 0 ? fslot : gslot) * cp_slot;
+        const char* src = cp_src + (size_t)kwr * cp_row;
         if (!perx) {
-            const int cs = isg ? gcs : scs;
-            bulk_g2s(dst + (cs - w0) * es, src + (size_t)cs * es, isg ? gbytes : sbytes, mb);
+            bulk_g2s(dst, src, cp_bytes, mb);
         } else {
+            const bool isg = cp_kind == 1;
+            const int es = isg ? (int)sizeof(TG) : (int)sizeof(R);
+            const int w0 = isg ? X0g : X0w;
             int c = w0;
             const int end = w0 + (isg ? NTG : NT);
             while (c < end) {
