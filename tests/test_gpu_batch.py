@@ -215,3 +215,42 @@ def test_batch_autotune_leaves_members_untouched():
         assert P.rel_err(f, fs) < 1e-6 and P.rel_err(g, gs) < 1e-6, (c.name, threads, rows, staged)
         assert d.step_count == 40
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_g16"])
+def test_staged_batch_matches_solo_bitwise(prec):
+    """A batch whose members all take the bulk-copy staged load path (no
+    walls; open x, or periodic x with nx a multiple of 8; widths that 216-column
+    strips cover with no more thread columns than 120-column ones) runs the
+    staged kernel over all members' work units in one launch per step. Each
+    member's populations equal those of its solo run on the same tile and
+    load path, bit for bit."""
+    import paper_2205_00686_gb300 as lbm
+    v = P.bc_variants()
+    specs = [(648, 96, "open_dirichlet"), (432, 64, "periodic"), (864, 40, "open_x_periodic_y"),
+             (216, 72, "periodic_flow_fixed_T")]
+    cases = [P.droplet_case(nx, ny, v[name], seed=41 + i) for i, (nx, ny, name) in enumerate(specs)]
+    b = lbm.Batch()
+    doms = []
+    for c in cases:
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec=prec)
+        d.init_fields(*c.fields())
+        b.attach(d)
+        doms.append(d)
+    threads, rows, staged = b.tile()
+    assert staged and threads == 224, (threads, rows, staged)
+    b.step(45)
+    assert b.sync() == 0
+    for c, d in zip(cases, doms):
+        b.detach(d)
+        f, g, Pp = d.populations()
+        s = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec=prec)
+        s.set_tile(threads, rows)
+        s.staged = True
+        s.init_fields(*c.fields())
+        s.step(45)
+        fs, gs, Ps = s.populations()
+        assert np.array_equal(f, fs) and np.array_equal(g, gs) and np.array_equal(Pp, Ps), c.name
+        assert d.step_count == 45
+        s.close()
+    b.close()
