@@ -91,8 +91,9 @@ struct WallRings {
 // needed only by stage A of its own row (three slots: the row being used, two
 // rows in flight); g and P^{n-1} stay in their slots until stages C and D5 of
 // the row, four iterations later (seven slots), which replaces the
-// per-column ring of the register-prefetch form.  After stage C reads
-// P^{n-1} of a row, that plane holds the row's g*_4.  g rows are kept in
+// per-column ring of the register-prefetch form; only stage C reads them
+// (stage D5 gets the row's g from C in registers), so no thread writes a
+// slot that a copy fills.  g rows are kept in
 // their storage type; FP16 rows are copied from the 8-column boundary at or
 // below the window start (16 bytes), so they carry 8 columns of slack.
 template <class TG>
@@ -112,7 +113,7 @@ struct StageSmem {
     typename Vec2<R>::T u[3][NT];
     R fs[3][9][NT];
     R gs[3][3][NT];
-    typename Vec2<R>::T own[5][NT];   // rho, then T (dp/dT)_rho -> g*_0 after stage C
+    typename Vec2<R>::T own[5][NT];   // rho and T (dp/dT)_rho, from stage A to stage C
     unsigned long long mbar[D + 1];
     unsigned long long probe;   // never armed: the wait-timeout test hook waits on it
     double red[NT / 32];
@@ -155,11 +156,11 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* m, unsigned parity
         : "memory");
     return ok != 0;
 }
-// generic-proxy shared-memory writes of this thread ordered before later
-// bulk copies into the same bytes
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
+// a product rounded on its own, never fused into a later add (a value that
+// one stage hands to another in a register then rounds as one passed through
+// shared memory)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 // bounded wait for an mbarrier phase: gives up after ~2^31 clocks (about a
 // second at the GB300's clock), records ERR_TIMEOUT and sets *stalled; a
 // thread that has stalled does not wait again on the same pipeline (its
@@ -247,6 +248,12 @@ struct Sweep {
     const char* cp_src;
     unsigned cp_dst, cp_slot, cp_row, cp_bytes;
     bool stalled;   // a staged-row wait ran out in this unit
+    // staged form: what stage D5 of a row uses from its own column stays in
+    // registers from stage C of that row (one iteration earlier) instead of
+    // shared memory: the row's g, rho, g*_0, g*_2 and g*_4 (c: written by
+    // C(k-3); d: read by D5(k-4)), and g*_2 of the row below (e)
+    R cg[5], crho, cgs0, cgs2, cgs4;
+    R dg[5], drho, dgs0, dgs2, dgs4, egs2;
 
     __device__ __forceinline__ Sweep(const Inst& I_, const Unit& U, const Phys<R>& P_, SM& S_,
                                      WallRings<R, NT>& WR_, unsigned mph0)
@@ -342,6 +349,10 @@ struct Sweep {
         irp = R(1);
         mass_acc = R(0);
         errbits = 0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) cg[q] = dg[q] = R(0);
+        crho = drho = R(1);
+        cgs0 = cgs2 = cgs4 = dgs0 = dgs2 = dgs4 = egs2 = R(0);
         // rotating ring slots: a0 = slot of row k, a1 = row k-1, a2 = row k-2
         // (ring of 3, so row k-3 is a0 again); b0 = slot of row k in the ring of 5
         ra0 = 0;
@@ -489,12 +500,11 @@ struct Sweep {
         const int bC = b0 >= 3 ? b0 - 3 : b0 + 2;   // slot5(k - 3)
         const int bD = b0 >= 4 ? b0 - 4 : b0 + 1;   // slot5(k - 4)
         const int kwn = (pery && kw == ny - 1) ? 0 : kw + 1;
-        // staged form: g/P slots of rows k - 3 and k - 4; the copies of row
-        // k + DA go out now, DA iterations before stage A needs them (the f
-        // slot they fill held row k - 1, the g/P slot row k - 5: both were
-        // last read before the previous iteration's closing barrier)
+        // staged form: g/P slot of row k - 3; the copies of row k + DA go out
+        // now, DA iterations before stage A needs them (the f slot they fill
+        // held row k - 1, the g/P slot row k - 5: both were last read before
+        // the previous iteration's closing barrier)
         const int gC = gq >= 3 ? gq - 3 : gq + NGS - 3;
-        const int gD = gq >= 4 ? gq - 4 : gq + NGS - 4;
         if constexpr (STG) {
             if (k + DA <= y1 + 3)
                 issue_row(k + DA, kw2, gq + DA >= NGS ? gq + DA - NGS : gq + DA,
@@ -568,7 +578,9 @@ struct Sweep {
                     // varsigma_3 = varsigma_4 = 1: m3* = w_dot (T + Qs), m4* = 0
                     const R TQ = Td + Qs;
                     const R a = R(0.25) * P.w_dot * TQ;
-                    gs0 = P.w5_0 * TQ;
+                    // unfused: stage D5 subtracts g_0 from g*_0, and the
+                    // staged form hands g*_0 over in a register
+                    gs0 = mul_rn(P.w5_0, TQ);
                     gs1 = a + h1;
                     gs2 = a + h2;
                     gs3 = a - h1;
@@ -584,24 +596,27 @@ struct Sweep {
                     gs3 = a - h1;
                     gs4 = b - h2;
                 }
-                // g*_1..3 are read by neighbours; g*_0 and g*_4 only by this
-                // column (rows r and r - 1 of stage D), so they go to the row's
-                // own slot in place of P^{n-1} and T (dp/dT)_rho
+                // g*_1 and g*_3 are read by the neighbour columns; g*_0, g*_2
+                // and g*_4 only by this column's stage D5 (rows r, r + 1 and
+                // r - 1).  The register-prefetch form keeps g*_2 in the gs
+                // ring and g*_0, g*_4 in the row's own slot in place of
+                // P^{n-1} and T (dp/dT)_rho
                 S.gs[a0][0][t] = gs1;
-                S.gs[a0][1][t] = gs2;
                 S.gs[a0][2][t] = gs3;
                 if constexpr (STG) {
-                    // g*_0 replaces T (dp/dT)_rho, g*_4 the consumed P^{n-1}.
-                    // g*_4 goes to position t, not sidx: at open x edges the
-                    // clamped halo columns (which run stage C in the steady
-                    // loop) share the edge column's sidx, while position t
-                    // is theirs alone (outside every valid column's sidx)
-                    R2 ow;
-                    ow.x = rho;
-                    ow.y = gs0;
-                    S.own[bC][t] = ow;
-                    S.pR[gC][t] = gs4;
+                    // the rest is read only by this column's D5 (rows r and
+                    // r + 1): registers
+                    cg[0] = g0;
+                    cg[1] = g1;
+                    cg[2] = g2;
+                    cg[3] = g3;
+                    cg[4] = g4;
+                    crho = rho;
+                    cgs0 = gs0;
+                    cgs2 = gs2;
+                    cgs4 = gs4;
                 } else {
+                    S.gs[a0][1][t] = gs2;
                     R4 oo;
                     oo.x = g4;
                     oo.y = rho;
@@ -642,6 +657,52 @@ struct Sweep {
                     for (int q = 0; q < 9; ++q) st_st(fw + q * plane, (TF)fo[q]);
                 }
             }
+        }
+
+        // ---- D5(k-4), staged form: rho c_v-weighted streaming of g* (Eq. 39).
+        // It runs in phase alpha: the g*_1, g*_3 it reads from the neighbour
+        // columns were written by C(k-4) before the last barrier, and the rest
+        // is this column's own, in registers (g*_4 of row k-3 from C(k-3) just
+        // above)
+        if constexpr (STG) {
+            const int r = k - 4;
+            if (STEADY || (r >= y0 && r < y1 && inD)) {
+                R go[5];
+                if (P.frozen_thermal) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) go[q] = dg[q];
+                } else {
+                    const bool vd = STEADY || tpery || r - 1 >= 0, vu = STEADY || tpery || r + 1 < ny;
+                    // thermal walls: halfway anti-bounce-back (Dirichlet) or
+                    // bounce-back (adiabatic) supplies the incoming g*
+                    R A1, A3;
+                    if (left_edge) A1 = dirW ? twW2 - S.gs[a1][2][t] : S.gs[a1][2][t];
+                    else A1 = S.gs[a1][0][xl1];
+                    if (right_edge) A3 = dirE ? twE2 - S.gs[a1][0][t] : S.gs[a1][0][t];
+                    else A3 = S.gs[a1][2][xr1];
+                    const R A2 = vd ? egs2 : (dirS ? twS2 - dgs4 : dgs4);
+                    const R A4 = vu ? cgs4 : (dirN ? twN2 - dgs2 : dgs2);
+                    const R iC = f_rcp(drho * P.cv);
+                    go[0] = dg[0] + (dgs0 - dg[0]) * iC;
+                    go[1] = dg[1] + (A1 - dg[1]) * iC;
+                    go[2] = dg[2] + (A2 - dg[2]) * iC;
+                    go[3] = dg[3] + (A3 - dg[3]) * iC;
+                    go[4] = dg[4] + (A4 - dg[4]) * iC;
+                }
+                if (inD) {
+                    TG* gw = gdst + (size_t)r * pitch + gx;
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) st_st(gw + q * plane, go[q]);
+                }
+            }
+            // row k-3 is the next D5's own row, row k-4 the row below it
+            egs2 = dgs2;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) dg[q] = cg[q];
+            drho = crho;
+            dgs0 = cgs0;
+            dgs2 = cgs2;
+            dgs4 = cgs4;
         }
 
         // ---- A(k): moments, EOS, psi
@@ -700,9 +761,6 @@ struct Sweep {
             // three rows above the segment)
             mass_acc += (inD && k >= y0 && k < y1) ? rho_a : R(0);
         }
-        // the g*_4 written over a staged P plane precedes the bulk copies that
-        // later refill that slot
-        if constexpr (STG) fence_proxy_async();
         __syncthreads();
 
         // ================= phase beta =================
@@ -862,26 +920,13 @@ struct Sweep {
             }
         }
 
-        // ---- D5(k-4): rho c_v-weighted streaming of g* (Eq. 39)
-        {
+        // ---- D5(k-4), register-prefetch form: rho c_v-weighted streaming of
+        // g* (Eq. 39)
+        if constexpr (!STG) {
             const int r = k - 4;
             if (STEADY || (r >= y0 && r < y1 && inD)) {
-                R4 o0, o1;
-                if constexpr (STG) {
-                    const TG* gr = &S.gR[gD][0][sidx + goff];
-                    o0.x = st_val(gr[0]);
-                    o0.y = st_val(gr[NTG]);
-                    o0.z = st_val(gr[2 * NTG]);
-                    o0.w = st_val(gr[3 * NTG]);
-                    o1.x = st_val(gr[4 * NTG]);
-                    const R2 ow = S.own[bD][t];
-                    o1.y = ow.x;
-                    o1.z = ow.y;
-                    o1.w = S.pR[gD][t];
-                } else {
-                    o0 = S.own[bD][0][t];
-                    o1 = S.own[bD][1][t];
-                }
+                const R4 o0 = S.own[bD][0][t];
+                const R4 o1 = S.own[bD][1][t];
                 R go[5];
                 if (P.frozen_thermal) {
                     go[0] = o0.x; go[1] = o0.y; go[2] = o0.z; go[3] = o0.w; go[4] = o1.x;
@@ -900,10 +945,7 @@ struct Sweep {
                     R A2, A4;
                     if (vd) A2 = S.gs[a2][1][t];
                     else A2 = dirS ? twS2 - o1.w : o1.w;
-                    if (vu) {
-                        if constexpr (STG) A4 = S.pR[gC][t];
-                        else A4 = S.own[bC][1][t].w;
-                    }
+                    if (vu) A4 = S.own[bC][1][t].w;
                     else A4 = dirN ? twN2 - gsc[1 * NT] : gsc[1 * NT];
                     const R A0 = o1.z;
                     const R iC = f_rcp(o1.y * P.cv);
