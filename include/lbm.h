@@ -308,10 +308,12 @@ int lbm_autotune(lbm_ctx* ctx, int steps_per_trial);
  * prescribes no implementation).  on = 1: each row of f, g and P^{n-1} that a
  * tile needs is brought into shared memory by bulk asynchronous copies
  * (cp.async.bulk, completion tracked by an mbarrier) two rows ahead of its
- * use; on = 0: each thread loads its own column a half row ahead into
- * registers.  Both paths do the same arithmetic in the same order; results
- * agree to rounding (the two kernels are compiled separately, so multiply-
- * adds may be contracted differently).  Staging needs LBM_FP32 or
+ * use (three on the 128- and 192-thread tiles); on = 0: each thread loads its
+ * own column a half row ahead into registers.  Both paths do the same
+ * arithmetic in the same order: with LBM_FP32 the populations are equal bit
+ * for bit; with LBM_FP32_G16 they agree to the FP16 rounding of a stored g
+ * (the kernels are compiled separately, and a multiply-add contracted
+ * differently can flip one such rounding).  Staging needs LBM_FP32 or
  * LBM_FP32_G16 and either open x edges or a periodic x axis with nx >= 32 a
  * multiple of 4 (LBM_FP32) or 8 (LBM_FP32_G16); lbm_create turns it on
  * (with a 224-thread tile) for wall-free domains wide enough for 216-column
