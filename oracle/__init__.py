@@ -24,6 +24,9 @@ LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
 PERIODIC, WALL, OPEN = 0, 1, 2
 T_PERIODIC, T_DIRICHLET, T_ADIABATIC = 0, 1, 2
 EDGE_W, EDGE_E, EDGE_S, EDGE_N = 0, 1, 2, 3
+# names of the per-node work arrays of orc_work, in the order of its codes
+WORK = ("rho", "T", "psi", "Fmx", "Fmy", "Fx", "Fy", "ux", "uy", "divu", "dTx", "dTy",
+        "Q", "Pn", "S", "fstar", "gstar", "ghost_psi_S", "ghost_psi_N")
 
 
 def build(force: bool = False) -> str:
@@ -115,6 +118,7 @@ def lib():
                                       ctypes.c_int, ctypes.POINTER(Diag)]
         L.orc_last_error.argtypes = [ctypes.c_void_p]
         L.orc_reconfigure.argtypes = [ctypes.c_void_p, P, B]
+        L.orc_work.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
         B3 = ctypes.POINTER(BC3)
         _i19 = ctypes.POINTER(ctypes.c_int)
         L.orc3_velocities.argtypes = [_i19, _i19, _i19, _dp]
@@ -351,6 +355,24 @@ class Sim:
         d = Diag()
         lib().orc_diagnostics(self._h, rho_l, rho_g, int(sessile), ctypes.byref(d))
         return {k: getattr(d, k) for k, _ in Diag._fields_}
+
+    def work(self, name: str) -> np.ndarray:
+        """One per-node quantity as the last step computed it (test hook):
+        rho, T, psi, Fmx, Fmy, Fx, Fy, ux, uy, divu, dTx, dTy, Q, Pn, S,
+        fstar [9][ny][nx], gstar [5][ny][nx], ghost_psi_S / ghost_psi_N [nx]."""
+        code = WORK.index(name)
+        if name == "fstar":
+            out = np.zeros((9, self.ny, self.nx))
+        elif name == "gstar":
+            out = np.zeros((5, self.ny, self.nx))
+        elif name.startswith("ghost"):
+            out = np.zeros(self.nx)
+        else:
+            out = np.zeros((self.ny, self.nx))
+        rc = lib().orc_work(self._h, code, _ptr(out))
+        if rc:
+            raise OracleError(rc)
+        return out
 
     @property
     def last_error(self) -> int:

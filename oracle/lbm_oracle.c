@@ -774,6 +774,39 @@ int orc_set_populations(orc_sim* s, const double* f, const double* g, const doub
     return ORC_OK;
 }
 
+/* test hook: a copy of one per-node quantity as the last step computed it
+ * (the phase that produced it is named beside each code in lbm_oracle.h) */
+int orc_work(const orc_sim* s, int which, double* out) {
+    if (!s || !out) return ORC_EINVAL;
+    const size_t N = (size_t)s->nx * s->ny;
+    const double* src = NULL;
+    size_t n = N;
+    switch (which) {
+        case ORC_W_RHO: src = s->rho; break;
+        case ORC_W_T: src = s->T; break;
+        case ORC_W_PSI: src = s->psi; break;
+        case ORC_W_FMX: src = s->Fmx; break;
+        case ORC_W_FMY: src = s->Fmy; break;
+        case ORC_W_FX: src = s->Fx; break;
+        case ORC_W_FY: src = s->Fy; break;
+        case ORC_W_UX: src = s->ux; break;
+        case ORC_W_UY: src = s->uy; break;
+        case ORC_W_DIVU: src = s->divu; break;
+        case ORC_W_DTX: src = s->dTx; break;
+        case ORC_W_DTY: src = s->dTy; break;
+        case ORC_W_Q: src = s->Q; break;
+        case ORC_W_PN: src = s->Pn; break;
+        case ORC_W_S: src = s->Stot; break;
+        case ORC_W_FSTAR: src = s->fs; n = 9 * N; break;
+        case ORC_W_GSTAR: src = s->gs; n = 5 * N; break;
+        case ORC_W_GHOST_PSI_S: src = s->gpsi_S; n = (size_t)s->nx; break;
+        case ORC_W_GHOST_PSI_N: src = s->gpsi_N; n = (size_t)s->nx; break;
+        default: return ORC_EINVAL;
+    }
+    memcpy(out, src, n * sizeof(double));
+    return ORC_OK;
+}
+
 long orc_step_count(const orc_sim* s) { return s ? s->step : -1; }
 int orc_last_error(const orc_sim* s) { return s ? s->err : ORC_EINVAL; }
 

@@ -122,6 +122,22 @@ int orc_get_populations(const orc_sim* s, double* f, double* g, double* P);
 int orc_set_populations(orc_sim* s, const double* f, const double* g, const double* P,
                         long step, double rho_ave_prev);
 long orc_step_count(const orc_sim* s);
+/* test hook: copies one per-node work array of the last step into out
+ * ([ny][nx]; [9][ny][nx] for f*, [5][ny][nx] for g*, [nx] for a ghost row).
+ * The values are those of the last orc_step (orc_fields and orc_diagnostics
+ * refresh the phase 1-4 arrays from the current state). */
+enum {
+    ORC_W_RHO = 0, ORC_W_T, ORC_W_PSI,     /* phases 1-2 */
+    ORC_W_FMX, ORC_W_FMY,                  /* phase 3, F_m (Eq. 9) */
+    ORC_W_FX, ORC_W_FY, ORC_W_UX, ORC_W_UY, /* phase 4, F_n and u (Eq. 11) */
+    ORC_W_DIVU,                            /* phase 5 */
+    ORC_W_DTX, ORC_W_DTY,                  /* phase 6, Eqs. 49-50 */
+    ORC_W_Q, ORC_W_PN, ORC_W_S,            /* phase 7: Q (Eq. 20), P^n, sum_i S_i (Eq. 24) */
+    ORC_W_FSTAR, ORC_W_GSTAR,              /* phases 8-9, post-collision populations */
+    ORC_W_GHOST_PSI_S, ORC_W_GHOST_PSI_N   /* Section 3.3 ghost rows of psi */
+};
+int orc_work(const orc_sim* s, int which, double* out);
+
 int orc_diagnostics(orc_sim* s, double rho_l, double rho_g, int sessile, orc_diag* d);
 int orc_last_error(const orc_sim* s);
 /* replaces params and boundary values between steps; the flow boundary kinds
