@@ -37,7 +37,18 @@
  * (frozen flow, rho c_v = 1), the exact Fourier amplification of the blend
  * and its continuum limit lambda k^2/(rho c_v), steady conduction, transient
  * conduction against its Fourier series, flat-interface coexistence, the
- * Laplace law, and the instability of the literal c_v = 0.1 reading.
+ * Laplace law, and the instability of the literal c_v = 0.1 reading.  The
+ * coupling terms (tests/test_oracle_coupling.py): compression heating of one
+ * step against -T (dp/dT) div u / (rho c_v), a sound wave on the adiabat at
+ * the adiabatic sound speed, the S history term keeping it there at every
+ * phase, an isobaric temperature wave decaying at lambda k^2 / (rho c_p) and
+ * advected at the flow speed, the local gradient of Eqs. 49-50 against the
+ * spectral gradient and exactly in steady conduction, and the source moments
+ * of Eq. 33.  The flow lattice (tests/test_oracle_transport.py): shear-wave
+ * and channel decay at nu k^2 (s_p, halfway bounce-back), the forcing of
+ * Eq. 8 against Guo's velocity-space term, the momentum gain F_n, and the
+ * Ding-Spelt ghost layer relaxing a droplet to 60 and 120 degrees.  The
+ * diagnostics against direct sums (tests/test_oracle_diagnostics.py).
  */
 #include "lbm_oracle.h"
 
