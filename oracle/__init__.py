@@ -20,6 +20,10 @@ _SRCS = [os.path.join(_HERE, "lbm_oracle.c"), os.path.join(_HERE, "lbm_oracle_an
          os.path.join(_HERE, "lbm_oracle3d.c")]
 _HDR = os.path.join(_HERE, "lbm_oracle.h")
 LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
+# the same sources built with -fopenmp: the per-node loops of a step run on
+# all host cores (OMP_NUM_THREADS); each node's arithmetic and every sum's
+# order are unchanged, so its results are bit-identical to the serial build
+LIB_OMP_PATH = os.path.join(_HERE, "liblbm_oracle_omp.so")
 
 PERIODIC, WALL, OPEN = 0, 1, 2
 T_PERIODIC, T_DIRICHLET, T_ADIABATIC = 0, 1, 2
@@ -29,17 +33,23 @@ WORK = ("rho", "T", "psi", "Fmx", "Fmy", "Fx", "Fy", "ux", "uy", "divu", "dTx", 
         "Q", "Pn", "S", "fstar", "gstar", "ghost_psi_S", "ghost_psi_N")
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+def _build_one(path: str, extra, force: bool) -> str:
     newest = max(os.path.getmtime(f) for f in _SRCS + [_HDR])
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
-        return LIB_PATH
-    tmp = LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c99", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC",
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= newest:
+        return path
+    tmp = path + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", *extra,
            "-shared", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction): the
+    serial library and its OpenMP build."""
+    _build_one(LIB_OMP_PATH, ["-fopenmp"], force)
+    return _build_one(LIB_PATH, [], force)
 
 
 class Params(ctypes.Structure):
@@ -81,16 +91,16 @@ class Component(ctypes.Structure):
                 ("touches_s", ctypes.c_int), ("touches_n", ctypes.c_int)]
 
 
-_lib = None
+_libs = {}
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
-def lib():
-    global _lib
-    if _lib is None:
+def lib(omp: bool = False):
+    """The serial oracle library, or (omp=True) its OpenMP build."""
+    if omp not in _libs:
         build()
-        L = ctypes.CDLL(LIB_PATH)
+        L = ctypes.CDLL(LIB_OMP_PATH if omp else LIB_PATH)
         P, B = ctypes.POINTER(Params), ctypes.POINTER(BC)
         L.orc_Tc.restype = ctypes.c_double
         L.orc_Tc.argtypes = [P]
@@ -147,8 +157,8 @@ def lib():
         L.orc_components.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_int, _ip,
                                      ctypes.POINTER(Component), ctypes.c_int, _ip]
-        _lib = L
-    return _lib
+        _libs[omp] = L
+    return _libs[omp]
 
 
 def _ptr(a: np.ndarray):
@@ -294,21 +304,23 @@ class OracleError(RuntimeError):
 
 
 class Sim:
-    """One FP64 CPU simulation of an nx x ny domain."""
+    """One FP64 CPU simulation of an nx x ny domain (omp=True: the OpenMP
+    build, same results on all host cores)."""
 
-    def __init__(self, nx: int, ny: int, params: dict, bc: dict):
+    def __init__(self, nx: int, ny: int, params: dict, bc: dict, omp: bool = False):
         self.nx, self.ny = nx, ny
+        self._L = lib(omp)
         self._p = make_params(params)
         self._b = make_bc(bc)
         err = ctypes.c_int(0)
-        self._h = lib().orc_create(nx, ny, ctypes.byref(self._p), ctypes.byref(self._b),
-                                   ctypes.byref(err))
+        self._h = self._L.orc_create(nx, ny, ctypes.byref(self._p), ctypes.byref(self._b),
+                                     ctypes.byref(err))
         if not self._h:
             raise OracleError(err.value)
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     __del__ = close
@@ -316,44 +328,44 @@ class Sim:
     def init(self, rho, ux, uy, T):
         arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.ny, self.nx)
                 for a in (rho, ux, uy, T)]
-        rc = lib().orc_init(self._h, *[_ptr(a) for a in arrs])
+        rc = self._L.orc_init(self._h, *[_ptr(a) for a in arrs])
         if rc:
             raise OracleError(rc)
 
     def step(self, n: int = 1, check: bool = True) -> int:
-        rc = lib().orc_step(self._h, int(n))
+        rc = self._L.orc_step(self._h, int(n))
         if rc and check:
             raise OracleError(rc)
         return rc
 
     @property
     def step_count(self) -> int:
-        return lib().orc_step_count(self._h)
+        return self._L.orc_step_count(self._h)
 
     def fields(self):
         out = [np.zeros((self.ny, self.nx)) for _ in range(4)]
-        lib().orc_fields(self._h, *[_ptr(a) for a in out])
+        self._L.orc_fields(self._h, *[_ptr(a) for a in out])
         return tuple(out)
 
     def populations(self):
         f = np.zeros((9, self.ny, self.nx))
         g = np.zeros((5, self.ny, self.nx))
         P = np.zeros((self.ny, self.nx))
-        lib().orc_get_populations(self._h, _ptr(f), _ptr(g), _ptr(P))
+        self._L.orc_get_populations(self._h, _ptr(f), _ptr(g), _ptr(P))
         return f, g, P
 
     def set_populations(self, f, g, P, step: int, rho_ave_prev: float):
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
         P = np.ascontiguousarray(P, dtype=np.float64)
-        rc = lib().orc_set_populations(self._h, _ptr(f), _ptr(g), _ptr(P), int(step),
+        rc = self._L.orc_set_populations(self._h, _ptr(f), _ptr(g), _ptr(P), int(step),
                                        float(rho_ave_prev))
         if rc:
             raise OracleError(rc)
 
     def diagnostics(self, rho_l: float, rho_g: float, sessile: bool = False) -> dict:
         d = Diag()
-        lib().orc_diagnostics(self._h, rho_l, rho_g, int(sessile), ctypes.byref(d))
+        self._L.orc_diagnostics(self._h, rho_l, rho_g, int(sessile), ctypes.byref(d))
         return {k: getattr(d, k) for k, _ in Diag._fields_}
 
     def work(self, name: str) -> np.ndarray:
@@ -369,19 +381,19 @@ class Sim:
             out = np.zeros(self.nx)
         else:
             out = np.zeros((self.ny, self.nx))
-        rc = lib().orc_work(self._h, code, _ptr(out))
+        rc = self._L.orc_work(self._h, code, _ptr(out))
         if rc:
             raise OracleError(rc)
         return out
 
     @property
     def last_error(self) -> int:
-        return lib().orc_last_error(self._h)
+        return self._L.orc_last_error(self._h)
 
     def reconfigure(self, params: dict, bc: dict):
         self._p = make_params(params)
         self._b = make_bc(bc)
-        rc = lib().orc_reconfigure(self._h, ctypes.byref(self._p), ctypes.byref(self._b))
+        rc = self._L.orc_reconfigure(self._h, ctypes.byref(self._p), ctypes.byref(self._b))
         if rc:
             raise OracleError(rc)
 

@@ -480,6 +480,7 @@ static void compute_macro(orc_sim* s) {
     const orc_params* p = &s->p;
 
     /* 1. rho = sum_i f_i (Eq. 11), T = sum_i g_i (Eq. 25) */
+#pragma omp parallel for schedule(static)
     for (size_t n = 0; n < N; ++n) {
         double r = 0.0, t = 0.0;
         for (int i = 0; i < 9; ++i) r += s->f[i * N + n];
@@ -488,15 +489,20 @@ static void compute_macro(orc_sim* s) {
         s->T[n] = t;
     }
     /* 2. psi = sqrt(2 (p_EOS - rho c_s^2) / G) */
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
     for (size_t n = 0; n < N; ++n) {
         double q = orc_psi2(p, s->rho[n], s->T[n]);
-        if (!(q >= 0.0)) s->err = ORC_EPSI;
+        if (!(q >= 0.0)) bad = 1;
         s->psi[n] = sqrt(q);
     }
+    if (bad) s->err = ORC_EPSI;
     /* wetting ghost layer, Section 3.3: rho_{x,0} = rho_{x,2} + tan(pi/2 -
      * theta) |rho_{x+1,1} - rho_{x-1,1}| where layer 1 is the fluid row next
-     * to the wall.  reading: the ghost temperature is the wall temperature
-     * (or the adjacent fluid temperature for an adiabatic wall). */
+     * to the wall.  reading: the ghost layer extends the fluid into the wall,
+     * so its psi is taken at the temperature of the fluid node next to it
+     * (layer 1), for every thermal wall kind; the wall temperature itself
+     * enters only the thermal lattice's anti-bounce-back. */
     for (int e = ORC_S; e <= ORC_N; ++e) {
         if (s->bc.flow[e] != ORC_WALL) continue;
         int y1 = e == ORC_S ? 0 : ny - 1;   /* paper's layer 1 */
@@ -506,7 +512,7 @@ static void compute_macro(orc_sim* s) {
             double rg = AT(s->rho, x, y2) +
                         s->cot_theta * fabs(AT(s->rho, ext_x(s, x + 1), y1) -
                                             AT(s->rho, ext_x(s, x - 1), y1));
-            double tg = s->bc.therm[e] == ORC_T_DIRICHLET ? wall_T(s, e, x) : AT(s->T, x, y1);
+            double tg = AT(s->T, x, y1);
             double q = orc_psi2(p, rg, tg);
             if (!(q >= 0.0)) s->err = ORC_EPSI;
             gp[x] = sqrt(q);
@@ -514,6 +520,7 @@ static void compute_macro(orc_sim* s) {
     }
     /* 3. F_m = -G psi(x) sum_{i=1..8} varpi(|c_i|^2) psi(x + c_i) c_i (Eq. 9),
      *    varpi(1) = 1/3, varpi(2) = 1/12 */
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double sx = 0.0, sy = 0.0;
@@ -530,6 +537,7 @@ static void compute_macro(orc_sim* s) {
     /* 4. F_n = F_m + F_b with F_b = (rho - rho_ave)(0, -g) (Section 4.3),
      *    rho u = sum_i c_i f_i + F_n / 2 (Eq. 11).  reading: rho_ave is the
      *    domain mean of the previous step's density. */
+#pragma omp parallel for schedule(static)
     for (size_t n = 0; n < N; ++n) {
         double fx = s->Fmx[n];
         double fy = s->Fmy[n] - (s->rho[n] - s->rho_ave_prev) * p->gravity;
@@ -565,6 +573,7 @@ static int one_step(orc_sim* s) {
 
     /* 5. div u.  reading: the isotropic central difference
      *    d_a phi = (1/c_s^2) sum_i w_i c_ia phi(x + c_i), D2Q9 weights. */
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double d = 0.0;
@@ -577,6 +586,7 @@ static int one_step(orc_sim* s) {
         }
     /* 6. grad T from local moments, Eqs. 49-50: cs2h d_x T = -vs1 m1^(1),
      *    with m1^(1) ~ m1 - m1^eq = m1 (m1^eq = 0, Eq. 47). */
+#pragma omp parallel for schedule(static)
     for (size_t n = 0; n < N; ++n) {
         double gl[5], m[5];
         for (int i = 0; i < 5; ++i) gl[i] = s->g[i * N + n];
@@ -588,6 +598,7 @@ static int one_step(orc_sim* s) {
      *    reading: d_t^2 T ~ (P^n - P^{n-1}) with P = Q / (rho c_v), which is
      *    d_t1 T by Eq. 34; the first step takes P^{-1} = P^0 (S = 0).
      *    S_i = w_i rho c_v (dt/2) d_t^2 T (Eq. 24). */
+#pragma omp parallel for schedule(static)
     for (size_t n = 0; n < N; ++n) {
         double C = s->rho[n] * p->cv;
         double q = -(C * (s->ux[n] * s->dTx[n] + s->uy[n] * s->dTy[n]) +
@@ -600,6 +611,7 @@ static int one_step(orc_sim* s) {
     }
     /* 8. D2Q9 MRT collision (Eq. 5) with the forcing of Eq. 8 */
     if (!p->frozen_flow) {
+#pragma omp parallel for schedule(static)
         for (size_t n = 0; n < N; ++n) {
             double fl[9], m[9], meq[9], F[9], ms[9], fo[9];
             for (int i = 0; i < 9; ++i) fl[i] = s->f[i * N + n];
@@ -627,6 +639,7 @@ static int one_step(orc_sim* s) {
     }
     /* 9. D2Q5 MRT collision (Eq. 39): m* = m - Lambda (m - m^eq) + Mh (G + S),
      *    m^eq = [T, 0, 0, w_dot T, 0] (Eq. 47), G_i = w_i Q (Eq. 23). */
+#pragma omp parallel for schedule(static)
     for (size_t n = 0; n < N; ++n) {
         double gl[5], m[5], src[5], msrc[5], ms[5], go[5];
         for (int i = 0; i < 5; ++i) gl[i] = s->g[i * N + n];
@@ -645,6 +658,7 @@ static int one_step(orc_sim* s) {
     if (!p->frozen_flow) {
         static const int OPP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
         for (int i = 0; i < 9; ++i)
+#pragma omp parallel for schedule(static)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
                     int sx = x - CX9[i], sy = y - CY9[i];
@@ -669,6 +683,7 @@ static int one_step(orc_sim* s) {
     {
         static const int OPP5[5] = {0, 3, 4, 1, 2};
         for (int i = 0; i < 5; ++i)
+#pragma omp parallel for schedule(static)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
                     size_t n = (size_t)y * nx + x;

@@ -352,8 +352,9 @@ static void macro3(orc3_sim* s) {
                     const double dx = s->rho[ID(wr(x + 1, nx), y, z1)] - s->rho[ID(wr(x - 1, nx), y, z1)];
                     const double dy = s->rho[ID(x, wr(y + 1, ny), z1)] - s->rho[ID(x, wr(y - 1, ny), z1)];
                     const double rg = s->rho[ID(x, y, z2)] + s->cot_theta * sqrt(dx * dx + dy * dy);
-                    const double tg = s->bc.therm[e] == ORC_T_DIRICHLET ? s->bc.T_edge[e]
-                                                                         : s->T[ID(x, y, z1)];
+                    /* reading: psi of the ghost at the temperature of
+                                     * the fluid node next to it (as in 2-D) */
+                    const double tg = s->T[ID(x, y, z1)];
                     const double q = orc_psi2(p, rg, tg);
                     if (!(q >= 0.0)) s->err = ORC_EPSI;
                     gp[(size_t)y * nx + x] = sqrt(q);

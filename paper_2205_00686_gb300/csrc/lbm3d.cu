@@ -219,7 +219,7 @@ __device__ R psi_nb(const Dom3& D, const Phys<R>& P, int x, int y, int z, int* e
     const R dx = rho[nid<R>(D, wrapn(x + 1, D.nx), y, z1)] - rho[nid<R>(D, wrapn(x - 1, D.nx), y, z1)];
     const R dy = rho[nid<R>(D, x, wrapn(y + 1, D.ny), z1)] - rho[nid<R>(D, x, wrapn(y - 1, D.ny), z1)];
     const R rg = rho[nid<R>(D, x, y, z2)] + (R)D.cot * rsq(dx * dx + dy * dy);
-    const R tg = D.therm[e] == T_DIRICHLET ? (R)D.T_edge[e] : A[A_T * D.plane + nid<R>(D, x, y, z1)];
+    const R tg = A[A_T * D.plane + nid<R>(D, x, y, z1)];   // the fluid node's temperature
     const R q2 = psi2_of(P, rg, tg);
     if (!(q2 >= R(0))) *err |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
     return f_sqrt(q2);
@@ -452,7 +452,7 @@ __device__ __forceinline__ void add_mass(const Dom3& D, double v, int slot) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((t & 31) == 0) red[t >> 5] = v;
     __syncthreads();
-    if (t == 0) atomicAdd(&D.ctl->mass[slot], red[0] + red[1] + red[2] + red[3]);
+    if (t == 0) massq_add(&D.ctl->massq[slot], red[0] + red[1] + red[2] + red[3], massq_scale(D.inv_n));
 }
 
 template <class R>
@@ -535,12 +535,14 @@ __global__ void __launch_bounds__(128) k3_macro(Dom3 D, Phys<R> P, int use_mass,
     if (use_mass) add_mass(D, in ? msum : 0.0, slot);
 }
 
-// end of a step: advance the counter and clear the density slot that the
-// step after next accumulates into
-__global__ void k3_advance(Ctl* ctl) {
-    const long long s = ctl->step + 1;
-    ctl->step = s;
-    ctl->mass[(s + 1) % 3] = 0.0;
+// end of a step: publish the density sum the step's blend accumulated (the
+// new state's, slot (s + 1) % 3), clear the slot the next step's blend
+// accumulates into and advance the counter
+__global__ void k3_advance(Ctl* ctl, double qscale) {
+    const long long s = ctl->step;
+    ctl->mass[(s + 1) % 3] = massq_value(ctl->massq[(s + 1) % 3], qscale);
+    ctl->massq[(s + 2) % 3] = 0;
+    ctl->step = s + 1;
 }
 
 // populations f = f^eq(rho, u), g = w^ T as deviations; P = 0
@@ -658,7 +660,7 @@ int launch_step(lbm3d_ctx* c) {
     k3_force<R><<<g, b, 0, c->stream>>>(c->D, P, L);
     k3_collide<R><<<g, b, 0, c->stream>>>(c->D, P, L);
     k3_blend<R><<<g, b, 0, c->stream>>>(c->D, P, L, c->params.gravity != 0.0);
-    k3_advance<<<1, 1, 0, c->stream>>>(c->ctl);
+    k3_advance<<<1, 1, 0, c->stream>>>(c->ctl, massq_scale(c->D.inv_n));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -832,11 +834,14 @@ int lbm3d_init_fields(lbm3d_ctx* c, const double* rho, const double* ux, const d
         k3_macro<float><<<g, b, 0, c->stream>>>(c->D, make_phys<float>(phys_of(c->params)), um, 0);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err3(c, e, "init kernels");
-    // step 0 reads the initial density sum from slot 2 ((0 - 1) mod 3)
+    // the initial density sum (accumulated into massq[0]) is read by step 0
+    // from slot 2 ((0 - 1) mod 3) and by step 1 from slot 0
     e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess && um) {
-        double m0 = 0.0;
-        e = cudaMemcpy(&m0, &c->ctl->mass[0], sizeof(double), cudaMemcpyDeviceToHost);
+        long long q0 = 0;
+        e = cudaMemcpy(&q0, &c->ctl->massq[0], sizeof(q0), cudaMemcpyDeviceToHost);
+        const double m0 = massq_value(q0, massq_scale(c->D.inv_n));
+        if (e == cudaSuccess) e = cudaMemcpy(&c->ctl->mass[0], &m0, sizeof(double), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(&c->ctl->mass[2], &m0, sizeof(double), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) return cuda_err3(c, e, "lbm3d_init_fields");

@@ -168,7 +168,7 @@ __global__ void k_fields_force(Inst I, PhysD p, Phys<float> pf, const Ctl* ctl, 
         if (kind == OPEN) return at(psi, xe, yy < 0 ? 0 : ny - 1);
         const int y1 = edge == ES ? 0 : ny - 1, y2 = edge == ES ? 1 : ny - 2;
         const C rg = at(rho, xe, y2) + cot * rabs(at(rho, extx(xe + 1), y1) - at(rho, extx(xe - 1), y1));
-        const C tg = I.therm[edge] == T_DIRICHLET ? (C)wall_T(I, edge, xe) : at(T, xe, y1);
+        const C tg = at(T, xe, y1);     // the fluid node's temperature
         if (sizeof(C) == 8) return (C)psi_of(p, (double)rg, (double)tg);
         return (C)f_sqrt(psi2_of(pf, (float)rg, (float)tg));
     };

@@ -21,13 +21,35 @@ enum { ERR_PSI = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
 // Device-resident control block of one domain: the device-side step counter
 // read by every launch, the three-slot ring of per-step density sums used by
 // the buoyancy force (step n accumulates sum rho(n) into slot n % 3 and reads
-// slot (n - 1) % 3), and the sticky error word.
+// slot (n - 1) % 3), and the sticky error word.  The CTAs of a launch add
+// their block sums as fixed-point integers (massq, see massq_scale), so the
+// total does not depend on the order in which the CTAs finish; the launch's
+// last CTA converts the finished slot to mass[] for the next step to read.
 struct Ctl {
     long long step;
     double mass[3];
+    long long massq[3];
     int err;
     int pad;
 };
+
+// fixed-point scale of Ctl::massq for a domain of N = 1 / inv_n nodes:
+// 2^(58 - e) with N < 2^e.  Densities stay below 16 (the EOS ends at 1/b =
+// 10.5), so a domain total stays below 2^62 and no sum overflows, while a
+// block sum keeps at least 30 fraction bits (N < 2^28) and small domains keep
+// the full double precision of their block sums
+__host__ __device__ __forceinline__ double massq_scale(double inv_n) {
+    int e = 0;
+    frexp(1.0 / inv_n, &e);
+    return ldexp(1.0, 58 - e);
+}
+__device__ __forceinline__ void massq_add(long long* slot, double block_sum, double scale) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(slot),
+              (unsigned long long)__double2ll_rn(block_sum * scale));
+}
+__host__ __device__ __forceinline__ double massq_value(long long q, double scale) {
+    return (double)q / scale;
+}
 
 // One domain as seen by the kernels.  Populations are stored as deviations
 // f_i - w_i rho_ref and g_i - w^_i T_ref, SoA planes [q][ny][pitch].

@@ -227,7 +227,7 @@ struct Sweep {
     bool colvalid, inB, inC, inD, left_edge, right_edge;
     bool dirW, dirE, dirS, dirN;
     int gx, gxl, xl1, xr1, cLL, cRR, cLR, cRL;
-    R twW2, twE2, twS2, twN2, TgS_l, TgS_c, TgS_r, TgN;
+    R twW2, twE2, twS2, twN2;
     // carried from A(k-1) to B(k-1), and the next row's loads
     R fp[9], rhop, rhodp, jxp, jyp, psip, irp;
     R fa[9], ga[5], pa;
@@ -319,7 +319,6 @@ struct Sweep {
         dirS = I.therm[ES] == T_DIRICHLET;
         dirN = I.therm[EN] == T_DIRICHLET;
         R twW = R(0), twE = R(0), twS = R(0), twN = R(0);
-        TgS_l = TgS_c = TgS_r = TgN = R(0);
         if (!tperx) {
             twW = (R)(I.T_edge[EW] - I.T_ref);
             twE = (R)(I.T_edge[EE] - I.T_ref);
@@ -327,15 +326,6 @@ struct Sweep {
         if (!tpery && inD) {
             twS = (R)(wall_T(I, ES, gx) - I.T_ref);
             twN = (R)(I.T_edge[EN] - I.T_ref);
-        }
-        if (wallS || wallN) {
-            // global columns of the window indices xl1, t, xr1
-            const int gl = perx ? wrapi(X - 1, nx) : xm1;
-            const int gr = perx ? wrapi(X + 1, nx) : xp1;
-            TgS_l = (R)wall_T(I, ES, gl);
-            TgS_c = (R)wall_T(I, ES, gx);
-            TgS_r = (R)wall_T(I, ES, gr);
-            TgN = (R)I.T_edge[EN];
         }
         twS2 = R(2) * P.w5_1 * twS;
         twN2 = R(2) * P.w5_1 * twN;
@@ -786,27 +776,26 @@ struct Sweep {
                     const int s = vd ? a2 : a1;
                     pSW = S.psi[s][xl1]; pS = S.psi[s][t]; pSE = S.psi[s][xr1];
                 } else {
-                    // south wall: layer 1 = row r (a1), layer 2 = row r + 1 (a0)
-                    const bool dr = I.therm[ES] == T_DIRICHLET;
+                    // south wall: layer 1 = row r (a1), layer 2 = row r + 1 (a0);
+                    // the ghost's psi at the temperature of the fluid node above it
                     pSW = ghost_psi(P, WR.rho[a0][xl1], WR.rho[a1][cLR], WR.rho[a1][cLL], cot,
-                                    dr ? TgS_l : WR.T[a1][xl1], &errbits);
+                                    WR.T[a1][xl1], &errbits);
                     pS = ghost_psi(P, WR.rho[a0][t], WR.rho[a1][xr1], WR.rho[a1][xl1], cot,
-                                   dr ? TgS_c : WR.T[a1][t], &errbits);
+                                   WR.T[a1][t], &errbits);
                     pSE = ghost_psi(P, WR.rho[a0][xr1], WR.rho[a1][cRR], WR.rho[a1][cRL], cot,
-                                    dr ? TgS_r : WR.T[a1][xr1], &errbits);
+                                    WR.T[a1][xr1], &errbits);
                 }
                 if (vu || !wallN) {
                     const int s = vu ? a0 : a1;
                     pNW = S.psi[s][xl1]; pN = S.psi[s][t]; pNE = S.psi[s][xr1];
                 } else {
                     // north wall: layer 1 = row r (a1), layer 2 = row r - 1 (a2)
-                    const bool dr = I.therm[EN] == T_DIRICHLET;
                     pNW = ghost_psi(P, WR.rho[a2][xl1], WR.rho[a1][cLR], WR.rho[a1][cLL], cot,
-                                    dr ? TgN : WR.T[a1][xl1], &errbits);
+                                    WR.T[a1][xl1], &errbits);
                     pN = ghost_psi(P, WR.rho[a2][t], WR.rho[a1][xr1], WR.rho[a1][xl1], cot,
-                                   dr ? TgN : WR.T[a1][t], &errbits);
+                                   WR.T[a1][t], &errbits);
                     pNE = ghost_psi(P, WR.rho[a2][xr1], WR.rho[a1][cRR], WR.rho[a1][cRL], cot,
-                                    dr ? TgN : WR.T[a1][xr1], &errbits);
+                                    WR.T[a1][xr1], &errbits);
                 }
                 // Eq. 9 with varpi(1) = 1/3, varpi(2) = 1/12
                 const R sx = (pE - pW) * R(1.0 / 3.0) + ((pNE - pSW) + (pSE - pNW)) * R(1.0 / 12.0);
@@ -1041,8 +1030,10 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
     }
 
     if (w.errbits) atomicOr(&I.ctl->err, w.errbits);
-    if (w.use_mass) {
+    {
         // block sum of this unit's output densities -> ring slot step % 3
+        // (kept with gravity off too, so that lbm_reconfigure can switch
+        // buoyancy on with the previous step's mean density in place)
         double macc = (double)w.mass_acc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) macc += __shfl_down_sync(0xffffffffu, macc, o);
@@ -1052,7 +1043,7 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
             double s = 0.0;
             for (int q = 0; q < NT / 32; ++q) s += S.red[q];
             const long long step = __ldcg(&I.ctl->step);
-            atomicAdd(&I.ctl->mass[step % 3], s);
+            massq_add(&I.ctl->massq[step % 3], s, massq_scale(I.inv_n));
         }
         __syncthreads();
     }
@@ -1088,14 +1079,16 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
         __threadfence();
         const unsigned done = atomicAdd(&L.sched[1], 1u);
         if (done == gridDim.x - 1) {
-            // every other CTA has finished: advance the domains' step counters,
-            // clear the density-sum slot the next step accumulates into, and
-            // reset the work counter for the next launch
+            // every other CTA has finished: publish this step's density sum,
+            // clear the slot the next step accumulates into, advance the
+            // domains' step counters and reset the work counter for the next
+            // launch
             __threadfence();
             for (int i = 0; i < L.n_inst; ++i) {
                 Ctl* c = L.insts[i].ctl;
                 const long long s = __ldcg(&c->step);
-                c->mass[(s + 1) % 3] = 0.0;
+                c->mass[s % 3] = massq_value(__ldcg(&c->massq[s % 3]), massq_scale(L.insts[i].inv_n));
+                c->massq[(s + 1) % 3] = 0;
                 c->step = s + 1;
             }
             L.sched[0] = 0u;
