@@ -68,7 +68,7 @@ def parse():
                          "autotuner's choice, else on where possible)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-instances", type=int, default=512)
-    ap.add_argument("--serve-steps", type=int, default=500)
+    ap.add_argument("--serve-steps", type=int, default=5000)
     ap.add_argument("--size", type=int, default=NX,
                     help="domain side (default 4096; smaller sides for profiler captures)")
     ap.add_argument("--ny", type=int, default=None,
@@ -186,21 +186,52 @@ def make_case(n=NX, ny=None):
     return W.open_evaporation(n, ny, R=640.0 * min(n, ny) / 4096.0, steps=0)
 
 
-def cpu_baseline(sample_n=1024, sample_steps=60):
-    """The FP64 C oracle, single-threaded, on a bounded sample of the
-    workload (a sample_n^2 domain of the same setup)."""
+def cpu_baseline(sample_n=1024, sample_steps=60, omp=False):
+    """The FP64 C oracle on a bounded sample of the workload (a sample_n^2
+    domain of the same setup): single-threaded, or (omp) its OpenMP build on
+    every host core, whose results are bit-identical."""
     import oracle
     c = make_case(sample_n)
-    s = oracle.Sim(c.nx, c.ny, c.params, c.bc)
+    s = oracle.Sim(c.nx, c.ny, c.params, c.bc, omp=omp)
     s.init(*c.fields())
     s.step(1)
     t0 = time.perf_counter()
     s.step(sample_steps)
     dt = time.perf_counter() - t0
     mlups = c.nx * c.ny * sample_steps / dt / 1e6
-    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%dx%d of the same setup, %d FP64 steps, %.1f s" % (
-                c.nx, c.ny, sample_steps, dt)}
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)) if omp else 1
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%dx%d of the same setup, %d FP64 steps, %.1f s%s" % (
+                c.nx, c.ny, sample_steps, dt, ", OpenMP over the per-node loops" if omp else "")}
+
+
+def fritz_check(gravities=(1e-5, 2e-5, 4e-5, 8e-5), max_steps=150000):
+    """Section 4.3: bubble departure from a 20-node heater at 1.1 T_c in a
+    300 x 600 pool started filled with saturated liquid, FP32; the departure
+    diameter per gravity (device-side region labelling every 200 steps) and
+    the log-log slope (Fritz: -1/2)."""
+    import paper_2205_00686_gb300 as lbm
+    from paper_2205_00686_gb300 import protocols as PR
+    from paper_2205_00686_gb300 import workloads as W
+
+    def make(g):
+        c = W.nucleate_boiling(300, 600, gravity=g, vapour_layer=False)
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+        d.init_fields(*c.fields())
+        return d
+
+    rg, rl = W.COEXISTENCE[0.86]
+    t0 = time.perf_counter()
+    out = PR.fritz_sweep(make, list(gravities), rl, rg, check_every=200, max_steps=max_steps,
+                         min_area=8)
+    rows = out["runs"]
+    return {"setup": "Section 4.3: 300x600 pool filled with saturated liquid, 20-node heater at "
+                     "1.1Tc, theta 75, lambda 2/3, open top, FP32",
+            "g": list(gravities),
+            "departure_step": [r["departure"]["step"] if r["departure"] else None for r in rows],
+            "D_d": [round(r["departure"]["diameter"], 2) if r["departure"] else None for r in rows],
+            "slope": round(out["slope"], 4) if out["slope"] is not None else None,
+            "fritz_slope": -0.5, "wall_s": round(time.perf_counter() - t0, 1)}
 
 
 def accuracy_check():
@@ -347,7 +378,7 @@ def batched_check(n_inst, steps, peak, warmup=3):
         doms.append(d)
     nodes = sum(c.nx * c.ny for c in cases)
 
-    def timed():
+    def timed(steps):
         b.step(warmup)
         b.sync()
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -362,15 +393,16 @@ def batched_check(n_inst, steps, peak, warmup=3):
         return ev0.elapsed_time(ev1) / 1e3
 
     tile0 = b.tile()
-    t0 = timed()
+    steps0 = min(steps, 500)
+    t0 = timed(steps0)
     tile = b.autotune(5)
-    t1 = timed()
+    t1 = timed(steps)
     out = {"instances": n_inst, "total_nodes": nodes, "steps": steps,
            "mlups": round(nodes * steps / t1 / 1e6, 1),
            "tile": [tile[0], tile[1]], "staged": tile[2],
            "hbm_frac_of_measured": round(BYTES_PER_NODE["fp32"] * nodes * steps / t1 / 1e9 / peak, 4),
            "default_tile": [tile0[0], tile0[1]], "default_staged": tile0[2],
-           "default_tile_mlups": round(nodes * steps / t0 / 1e6, 1)}
+           "default_tile_mlups": round(nodes * steps0 / t0 / 1e6, 1)}
     b.close()
     for d in doms:
         d.close()
@@ -530,13 +562,15 @@ def run_ours(args):
         extras["d2_law"] = d2_law_check()
         extras["d2_open_outflow"] = d2_open_check()
         extras["error_vs_fp64"] = accuracy_check()
+        extras["fritz"] = fritz_check()
         if not args.no_serve:
-            extras["batched"] = batched_check(args.serve_instances, 200, peak)
+            extras["batched"] = batched_check(args.serve_instances, args.serve_steps, peak)
             extras["served"] = served_check(args.serve_instances, args.serve_steps)
 
-    cpu = None
+    cpu = cpu_omp = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+        cpu_omp = cpu_baseline(sample_steps=300, omp=True)
 
     line = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
@@ -552,7 +586,8 @@ def run_ours(args):
                          % (BYTES_PER_NODE[args.prec] * N / 2 ** 30),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "tile": list(dom.tile()), "staged": dom.staged},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+        "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_omp,
+        "e2e": e2e, "clocks": clk.summary(),
         "gpu_launches": args.steps,
         **extras,
     }
@@ -590,8 +625,10 @@ def run_reference(args):
         "n_gpus": world, "steps": steps, "warmup": args.warmup,
         "ms_per_step": round(dt / steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "droplet evaporation, open outflow, Dirichlet 0.95Tc edges, "
-                               "R=640, 4096x4096, FP32 fused step", "nx": NX, "ny": NY},
+        "config": {"workload": "FP64 CPU oracle (single thread) on a %dx%d sample of the "
+                               "droplet evaporation setup (open outflow, Dirichlet 0.95Tc edges, "
+                               "R=%g)" % (c.nx, c.ny, 640.0 * c.nx / 4096.0),
+                   "nx": c.nx, "ny": c.ny, "sample_of": "%dx%d" % (NX, NY)},
         "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,

@@ -126,7 +126,12 @@ int lbm_default_params(lbm_params* p);
  * (both ping-pong copies of f, g and P).  Returns 0 for invalid sizes. */
 size_t lbm_state_bytes(int nx, int ny, int prec);
 
-/* Creates a simulation context.
+/* Creates a simulation context: one nx x ny domain of the coupled problem of
+ * Section 2 (D2Q9 flow lattice, Peng-Robinson EOS, Eqs. 1-11) and Section 3.2
+ * (D2Q5 temperature lattice, Eqs. 39-40), with the boundaries of Sections
+ * 3.3 and 4 (periodic, halfway bounce-back walls with the wetting ghost
+ * layer, open edges, Dirichlet / adiabatic / heater temperatures) given in
+ * lbm_bc, the model constants of Section 4 in lbm_params.
  *  stream: a cudaStream_t (as void*) to queue work on, or NULL for a stream
  *          the library creates and owns.  The legacy default stream cannot be
  *          captured into CUDA graphs; pass a created stream.
@@ -148,6 +153,12 @@ int lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* ux, const dou
                     const double* T);
 
 /* Queues n coupled time steps (n >= 0), asynchronous on the context stream.
+ * One step is the paper's full update: moments (Eqs. 11, 25), EOS and psi
+ * (Eq. 10), the interaction force (Eq. 9) with the buoyancy of Section 4.3,
+ * the D2Q9 MRT collision with the forcing of Eq. 8 (Eqs. 5, 7) and pull
+ * streaming (Eq. 6), the source Q of Eq. 20 with the local gradient of
+ * Eqs. 49-50 and S of Eq. 24, the D2Q5 MRT collision and the rho c_v-weighted
+ * streaming of Eq. 39.
  * Returns LBM_ESTATE before initialisation, LBM_ECUDA on launch failure; a
  * sticky device error from an earlier step is returned without queuing. */
 int lbm_step(lbm_ctx* ctx, int n);
@@ -182,7 +193,10 @@ int lbm_sync(lbm_ctx* ctx);
 
 /* Checkpoint: a raw binary of the current-state device buffers, the step
  * counter, the buoyancy mass history, params and bc, with a header and a
- * CRC-32.  lbm_load requires a context of the same nx, ny and precision and
+ * CRC-32.  The paper has no counterpart (it prescribes no implementation);
+ * what is saved is the full state the time step of Eqs. 5-6 and 39 reads:
+ * f, g, the P^{n-1} history behind S of Eq. 24, and the previous step's
+ * density sum behind rho_ave of Section 4.3.  lbm_load requires a context of the same nx, ny and precision and
  * restores it bit for bit.  Both synchronise.  LBM_EIO on file errors or a
  * CRC / header mismatch. */
 int lbm_save(lbm_ctx* ctx, const char* path);

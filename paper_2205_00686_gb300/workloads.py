@@ -186,11 +186,18 @@ def heated_surface(nx=400, ny=200, R=50.0, w=5.0, T_sat=0.86, T_wall=0.95, theta
 
 
 def nucleate_boiling(nx=300, ny=600, gravity=2e-5, heater_w=20, T_sat=0.86, T_h=1.1,
-                     theta=75.0, amp=1e-3, seed=4, steps=60000, p=None) -> Case:
+                     theta=75.0, amp=1e-3, seed=4, steps=60000, p=None,
+                     vapour_layer=True) -> Case:
     """Pool boiling (Section 4.3 shape): liquid pool on a wall with a central
-    heater segment, vapour layer in the top sixth, buoyancy (rho-rho_ave)g."""
+    heater segment, buoyancy (rho-rho_ave)g, open top.  With vapour_layer the
+    top sixth starts as vapour (the benchmark configuration's pool); without
+    it the enclosure starts filled with saturated liquid, as Section 4.3
+    states."""
     rg, rl = COEXISTENCE[T_sat]
-    rho = tanh_layer(nx, ny, 5.0 * ny / 6.0, 4.0, rl, rg)
+    if vapour_layer:
+        rho = tanh_layer(nx, ny, 5.0 * ny / 6.0, 4.0, rl, rg)
+    else:
+        rho = np.full((ny, nx), rl)
     if amp:
         rho = rho + noise(seed, (ny, nx), amp)
     T = np.full((ny, nx), T_sat * TC)
@@ -200,7 +207,8 @@ def nucleate_boiling(nx=300, ny=600, gravity=2e-5, heater_w=20, T_sat=0.86, T_h=
                  [T_PERIODIC, T_PERIODIC, T_DIRICHLET, T_DIRICHLET],
                  T_edge=[0.0, 0.0, T_sat * TC, T_sat * TC], theta_deg=theta,
                  heater=(x0, x0 + heater_w), T_heater=T_h * TC)
-    return Case("nucleate_boiling_%dx%d_g%g" % (nx, ny, gravity), nx, ny,
+    return Case("nucleate_boiling_%dx%d_g%g%s" % (nx, ny, gravity, "" if vapour_layer else "_liquid"),
+                nx, ny,
                 p or params(lambda_=2.0 / 3.0, gravity=gravity), bc, rho, z, z.copy(), T,
                 steps, rl, rg)
 

@@ -254,3 +254,71 @@ def test_staged_batch_matches_solo_bitwise(prec):
         assert d.step_count == 45
         s.close()
     b.close()
+
+
+@pytest.mark.parametrize("staged_set", [False, True])
+def test_gravity_batch_matches_solo_bitwise(staged_set):
+    """With buoyancy on, each step reads the mean density of the previous
+    step (reading R16).  The CTAs add their block sums of it as fixed-point
+    integers, so the sum does not depend on which CTA finishes first: a
+    member of a batch gets, bit for bit, the populations of its solo run on
+    the same tile, and a rerun repeats them exactly."""
+    import paper_2205_00686_gb300 as lbm
+    v = P.bc_variants()
+    if staged_set:
+        specs = [(648, 96, "open_dirichlet"), (432, 64, "periodic"), (864, 40, "open_x_periodic_y")]
+    else:
+        specs = [(100, 80, "open_dirichlet"), (257, 129, "wall_open_heater"),
+                 (33, 47, "two_walls_adiabatic"), (130, 200, "open_x_walls_y")]
+    cases = [P.droplet_case(nx, ny, v[name], seed=51 + i, gravity=3e-5)
+             for i, (nx, ny, name) in enumerate(specs)]
+    b = lbm.Batch()
+    doms = []
+    for c in cases:
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+        d.init_fields(*c.fields())
+        b.attach(d)
+        doms.append(d)
+    threads, rows, staged = b.tile()
+    assert bool(staged) == staged_set, (threads, rows, staged)
+    b.step(70)
+    assert b.sync() == 0
+    for c, d in zip(cases, doms):
+        b.detach(d)
+        got = d.populations()
+        runs = []
+        for _ in range(2):
+            s = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+            s.set_tile(threads, rows)
+            s.staged = bool(staged)
+            s.init_fields(*c.fields())
+            s.step(70)
+            runs.append(s.populations())
+            s.close()
+        for a, r1, r2 in zip(got, runs[0], runs[1]):
+            assert np.array_equal(r1, r2), c.name        # rerun: identical
+            assert np.array_equal(a, r1), c.name         # batch member = solo
+        d.close()
+    b.close()
+
+
+def test_reconfigure_switches_buoyancy_on_with_the_last_mean_density():
+    """Gravity switched on between steps (lbm_reconfigure) takes the previous
+    step's mean density at once, as the oracle does (FP64, 1e-12)."""
+    import oracle
+    import paper_2205_00686_gb300 as lbm
+    c = P.droplet_case(90, 70, P.bc_variants()["wall_open_heater"], seed=61)
+    d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp64")
+    d.init_fields(*c.fields())
+    o = oracle.Sim(c.nx, c.ny, c.params, c.bc)
+    o.init(*c.fields())
+    d.step(25)
+    o.step(25)
+    p2 = dict(c.params, gravity=4e-5)
+    d.reconfigure(p2, c.bc)
+    o.reconfigure(p2, c.bc)
+    d.step(25)
+    o.step(25)
+    fe = P.field_errors(d.get_rho_u_T(), o.fields())
+    assert max(fe.values()) <= 1e-12, fe
+    d.close()
