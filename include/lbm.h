@@ -282,11 +282,26 @@ int lbm_regions(lbm_ctx* ctx, double threshold, int below, int* labels, lbm_regi
 
 /* stream: as in lbm_create. */
 int lbm_batch_create(void* stream, lbm_batch** out);
-/* Adds / removes a context (synchronising the batch stream first).  A
- * context belongs to at most one batch. LBM_EINVAL on precision or
- * parameter mismatch. */
+/* Adds / removes a context.  A context belongs to at most one batch.
+ * LBM_EINVAL on precision or parameter mismatch.  Neither call waits on the
+ * host for queued work: attach makes the batch stream wait for the work
+ * queued so far on the context's stream (its initialisation), detach makes
+ * the context's stream wait for the batch steps queued so far, so what the
+ * context does next on its own stream (readback, destroy) sees their result.
+ * The batch's instance table and work list are rebuilt in stream order
+ * (freed and allocated on the batch stream), so launches already queued
+ * keep theirs. */
 int lbm_batch_attach(lbm_batch* b, lbm_ctx* ctx);
 int lbm_batch_detach(lbm_batch* b, lbm_ctx* ctx);
+/* Queues, on the batch stream, a copy of every attached context's sticky
+ * device error word (LBM error bits; 0 = none) into host_out[i], i in
+ * attach order (the order the batch lists its members), for
+ * lbm_batch_size(b) ints.  host_out must be page-locked (pinned) host memory
+ * and is valid once the batch stream has passed this point (an event
+ * recorded after the call).  Lets a scheduler check a chunk of steps for
+ * errors without waiting for the chunks queued after it.  The paper has no
+ * counterpart. */
+int lbm_batch_errors_async(lbm_batch* b, int* host_out);
 /* Number of attached contexts. */
 int lbm_batch_size(const lbm_batch* b);
 /* Queues n steps of every attached context on the batch stream. */

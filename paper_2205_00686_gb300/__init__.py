@@ -38,6 +38,7 @@ ABI_FUNCTIONS = (
     "lbm_step_count", "lbm_sync", "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
     "lbm_batch_create", "lbm_batch_attach", "lbm_batch_detach", "lbm_batch_size",
     "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy", "lbm_batch_autotune",
+    "lbm_batch_errors_async",
     "lbm_batch_get_tile", "lbm_set_tile", "lbm_get_tile",
     "lbm_autotune", "lbm_set_staging", "lbm_get_staging", "lbm_set_wait_probe",
     "lbm_diag_reduce_noalloc", "lbm_reconfigure", "lbm_contact_angle",
@@ -133,6 +134,7 @@ def lib():
             "lbm_batch_size": ([_vp], ctypes.c_int),
             "lbm_batch_step": ([_vp, ctypes.c_int], ctypes.c_int),
             "lbm_batch_sync": ([_vp], ctypes.c_int),
+            "lbm_batch_errors_async": ([_vp, _vp], ctypes.c_int),
             "lbm_batch_destroy": ([_vp], None),
             "lbm_batch_autotune": ([_vp, ctypes.c_int], ctypes.c_int),
             "lbm_batch_get_tile": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -479,6 +481,12 @@ class Batch:
 
     def sync(self):
         return lib().lbm_batch_sync(self._h)
+
+    def errors_async(self, host_ptr: int):
+        """Queues a copy of the members' error words (attach order) into the
+        pinned host buffer at host_ptr (len(self) int32); valid once the
+        batch stream has passed this point."""
+        _check(lib().lbm_batch_errors_async(self._h, ctypes.c_void_p(host_ptr)))
 
     def autotune(self, steps_per_trial: int = 5):
         """Times load path x threads x rows on a shadow batch of the members'

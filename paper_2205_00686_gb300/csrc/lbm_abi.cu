@@ -239,6 +239,15 @@ struct lbm_batch {
     PhysD phys;
     lbm_params params;
     cudaGraphExec_t graph = nullptr;
+    int* err_dev = nullptr;            // members' error words, gathered by lbm_batch_errors_async
+    // pinned staging ring for the unit-list uploads of batch_rebuild: a slot
+    // is reused only after its previous upload (event) has completed, so a
+    // rebuild never waits for the work already queued on the batch stream
+    static constexpr int kStage = 4;
+    void* stage[kStage] = {};
+    size_t stage_bytes[kStage] = {};
+    cudaEvent_t stage_ev[kStage] = {};
+    int stage_next = 0;
 };
 
 // a context attached to a batch is stepped on the batch's stream: wait for it
@@ -1067,12 +1076,19 @@ int lbm_autotune(lbm_ctx* c, int steps) {
 }
 
 // ---- batch ---------------------------------------------------------------
+// Rebuilds the batch's instance table and work-unit list after a member
+// joined or left.  Stream-ordered: the old device arrays are freed, and the
+// new ones allocated and filled, on the batch stream (cudaFreeAsync,
+// cudaMallocAsync, copies from a pinned staging slot), so launches already
+// queued keep their own arrays and the host does not wait for them.
 static int batch_rebuild(lbm_batch* b) {
     drop_graph(&b->graph);
-    if (b->insts) cudaFree(b->insts);
-    if (b->units) cudaFree(b->units);
+    if (b->insts) cudaFreeAsync(b->insts, b->stream);
+    if (b->units) cudaFreeAsync(b->units, b->stream);
+    if (b->err_dev) cudaFreeAsync(b->err_dev, b->stream);
     b->insts = nullptr;
     b->units = nullptr;
+    b->err_dev = nullptr;
     b->n_units = 0;
     if (b->members.empty()) return LBM_OK;
     std::vector<Inst> hi;
@@ -1105,10 +1121,34 @@ static int batch_rebuild(lbm_batch* b) {
     // keep domain order, so neighbouring units share halos in L2
     std::stable_sort(us.begin(), us.end(),
                      [](const Unit& a, const Unit& b) { return a.y1 - a.y0 > b.y1 - b.y0; });
-    cudaError_t e = cudaMalloc(&b->insts, hi.size() * sizeof(Inst));
-    if (e == cudaSuccess) e = cudaMalloc(&b->units, us.size() * sizeof(Unit));
-    if (e == cudaSuccess) e = cudaMemcpy(b->insts, hi.data(), hi.size() * sizeof(Inst), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->units, us.data(), us.size() * sizeof(Unit), cudaMemcpyHostToDevice);
+    const size_t bi = hi.size() * sizeof(Inst), bu = us.size() * sizeof(Unit);
+    const size_t off_u = round_up(bi, kAlign), need = off_u + bu;
+    const int slot = b->stage_next;
+    b->stage_next = (slot + 1) % lbm_batch::kStage;
+    cudaError_t e = cudaSuccess;
+    if (b->stage_ev[slot]) e = cudaEventSynchronize(b->stage_ev[slot]);
+    else e = cudaEventCreateWithFlags(&b->stage_ev[slot], cudaEventDisableTiming);
+    if (e == cudaSuccess && b->stage_bytes[slot] < need) {
+        if (b->stage[slot]) cudaFreeHost(b->stage[slot]);
+        b->stage[slot] = nullptr;
+        b->stage_bytes[slot] = 0;
+        e = cudaMallocHost(&b->stage[slot], need);
+        if (e == cudaSuccess) b->stage_bytes[slot] = need;
+    }
+    if (e == cudaSuccess) {
+        char* st = (char*)b->stage[slot];
+        memcpy(st, hi.data(), bi);
+        memcpy(st + off_u, us.data(), bu);
+        e = cudaMallocAsync((void**)&b->insts, bi, b->stream);
+    }
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->units, bu, b->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&b->err_dev, hi.size() * sizeof(int), b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->insts, b->stage[slot], bi, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->units, (char*)b->stage[slot] + off_u, bu, cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->stage_ev[slot], b->stream);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
     b->n_units = (int)us.size();
     int ctas = 1;
@@ -1116,6 +1156,24 @@ static int batch_rebuild(lbm_batch* b) {
     step_occupancy(b->prec, b->threads, b->walls, b->staged, &ctas, &smem);
     b->grid = (int)std::min<long long>((long long)b->n_units, (long long)std::max(ctas, 1) * num_sms());
     return LBM_OK;
+}
+
+// makes `waiter` wait for the work queued so far on `first` (no host wait)
+static cudaError_t stream_after(cudaStream_t waiter, cudaStream_t first) {
+    if (waiter == first) return cudaSuccess;
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev, first);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(waiter, ev, 0);
+    cudaEventDestroy(ev);
+    return e;
+}
+
+// error words of a batch's members (attach order) -> out
+__global__ void k_gather_err(const Inst* insts, int n, int* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = insts[i].ctl->err;
 }
 
 int lbm_batch_create(void* stream, lbm_batch** out) {
@@ -1153,8 +1211,10 @@ int lbm_batch_attach(lbm_batch* b, lbm_ctx* c) {
     } else if (b->prec != c->prec || !same_physics(b->params, c->params)) {
         return set_err(c, LBM_EINVAL, "batch members must share precision and physics");
     }
-    cudaStreamSynchronize(c->stream);
-    cudaStreamSynchronize(b->stream);
+    // the batch stream waits for the context's queued work (its
+    // initialisation); the host waits for neither stream
+    cudaError_t e = stream_after(b->stream, c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "lbm_batch_attach");
     b->members.push_back(c);
     c->batch = b;
     int rc = batch_rebuild(b);
@@ -1168,10 +1228,24 @@ int lbm_batch_attach(lbm_batch* b, lbm_ctx* c) {
 
 int lbm_batch_detach(lbm_batch* b, lbm_ctx* c) {
     if (!b || !c || c->batch != b) return LBM_EINVAL;
-    cudaStreamSynchronize(b->stream);
+    // the context's own stream waits for the batch's steps queued so far, so
+    // whatever it does next sees the state they leave; the host does not wait
+    cudaError_t e = stream_after(c->stream, b->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "lbm_batch_detach");
     b->members.erase(std::remove(b->members.begin(), b->members.end(), c), b->members.end());
     c->batch = nullptr;
     return batch_rebuild(b);
+}
+
+int lbm_batch_errors_async(lbm_batch* b, int* host_out) {
+    if (!b || !host_out) return LBM_EINVAL;
+    const int n = (int)b->members.size();
+    if (n == 0) return LBM_OK;
+    k_gather_err<<<(n + 127) / 128, 128, 0, b->stream>>>(b->insts, n, b->err_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_out, b->err_dev, n * sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
 int lbm_batch_size(const lbm_batch* b) { return b ? (int)b->members.size() : 0; }
@@ -1302,8 +1376,16 @@ void lbm_batch_destroy(lbm_batch* b) {
     for (lbm_ctx* c : b->members) c->batch = nullptr;
     b->members.clear();
     drop_graph(&b->graph);
-    if (b->insts) cudaFree(b->insts);
-    if (b->units) cudaFree(b->units);
+    if (b->stream) {
+        if (b->insts) cudaFreeAsync(b->insts, b->stream);
+        if (b->units) cudaFreeAsync(b->units, b->stream);
+        if (b->err_dev) cudaFreeAsync(b->err_dev, b->stream);
+        cudaStreamSynchronize(b->stream);
+    }
+    for (int k = 0; k < lbm_batch::kStage; ++k) {
+        if (b->stage[k]) cudaFreeHost(b->stage[k]);
+        if (b->stage_ev[k]) cudaEventDestroy(b->stage_ev[k]);
+    }
     if (b->sched) cudaFree(b->sched);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;

@@ -69,7 +69,6 @@ struct StepSmem {
     // per column and row: g_dev[0..4], rho, then P^{n-1} and T (dp/dT)_rho,
     // which stage C replaces by the row's post-collision g*_0 and g*_4
     typename Vec4<R>::T own[5][2][NT];
-    double red[NT / 32];
     int unit;
 };
 
@@ -116,7 +115,6 @@ struct StageSmem {
     typename Vec2<R>::T own[5][NT];   // rho and T (dp/dT)_rho, from stage A to stage C
     unsigned long long mbar[D + 1];
     unsigned long long probe;   // never armed: the wait-timeout test hook waits on it
-    double red[NT / 32];
     int unit;
 };
 
@@ -1031,21 +1029,17 @@ __device__ __forceinline__ void process_unit(const Inst& I, const Unit& U,
 
     if (w.errbits) atomicOr(&I.ctl->err, w.errbits);
     {
-        // block sum of this unit's output densities -> ring slot step % 3
-        // (kept with gravity off too, so that lbm_reconfigure can switch
-        // buoyancy on with the previous step's mean density in place)
+        // warp sums of this unit's output densities -> ring slot step % 3, as
+        // fixed-point integers (order-free, so no barrier is needed); kept
+        // with gravity off too, so that lbm_reconfigure can switch buoyancy on
+        // with the previous step's density sum in place
         double macc = (double)w.mass_acc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) macc += __shfl_down_sync(0xffffffffu, macc, o);
-        if ((w.t & 31) == 0) S.red[w.t >> 5] = macc;
-        __syncthreads();
-        if (w.t == 0) {
-            double s = 0.0;
-            for (int q = 0; q < NT / 32; ++q) s += S.red[q];
+        if ((w.t & 31) == 0) {
             const long long step = __ldcg(&I.ctl->step);
-            massq_add(&I.ctl->massq[step % 3], s, massq_scale(I.inv_n));
+            massq_add(&I.ctl->massq[step % 3], macc, massq_scale(I.inv_n));
         }
-        __syncthreads();
     }
 }
 
@@ -1075,22 +1069,29 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
         const Unit U = L.units[u];
         process_unit<PREC, NT, UNIT, STG>(L.insts[U.inst], U, P, S, WR, mph, L.wait_probe);
     }
+    // the last CTA to finish (its thread 0 finds the finished-CTA count at
+    // gridDim.x - 1; S.unit is free once the unit loop has ended) publishes
+    // each domain's density sum, clears the slot the next step accumulates
+    // into, advances the step counters and resets the work counters for the
+    // next launch; its threads share the domains, so a batch of hundreds of
+    // domains costs a few dependent loads per thread, not per domain
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned done = atomicAdd(&L.sched[1], 1u);
-        if (done == gridDim.x - 1) {
-            // every other CTA has finished: publish this step's density sum,
-            // clear the slot the next step accumulates into, advance the
-            // domains' step counters and reset the work counter for the next
-            // launch
-            __threadfence();
-            for (int i = 0; i < L.n_inst; ++i) {
-                Ctl* c = L.insts[i].ctl;
-                const long long s = __ldcg(&c->step);
-                c->mass[s % 3] = massq_value(__ldcg(&c->massq[s % 3]), massq_scale(L.insts[i].inv_n));
-                c->massq[(s + 1) % 3] = 0;
-                c->step = s + 1;
-            }
+        S.unit = done == gridDim.x - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    if (S.unit) {
+        __threadfence();
+        for (int i = threadIdx.x; i < L.n_inst; i += NT) {
+            Ctl* c = L.insts[i].ctl;
+            const long long s = __ldcg(&c->step);
+            c->mass[s % 3] = massq_value(__ldcg(&c->massq[s % 3]), massq_scale(L.insts[i].inv_n));
+            c->massq[(s + 1) % 3] = 0;
+            c->step = s + 1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
             L.sched[0] = 0u;
             L.sched[1] = 0u;
             __threadfence();

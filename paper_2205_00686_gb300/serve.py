@@ -15,7 +15,10 @@ server
 * between chunks of steps, retires the domains that reached their target,
   copies their fields to the host, frees their memory and admits new
   requests into the freed space (continuous batching: no request waits for
-  the whole batch to finish);
+  the whole batch to finish).  The loop is pipelined: the next chunk is
+  queued before the host waits for the previous one, and admission and
+  read-back run on each domain's own stream, so the device is not left idle
+  while the host schedules;
 * records, per request, the time from arrival to completion, and overall
   the aggregate node updates per second.
 
@@ -48,7 +51,8 @@ class Request:
     finished: Optional[float] = None
     result: Optional[tuple] = None      # (rho, ux, uy, T) host arrays
     error: int = 0
-    done_steps: int = 0
+    done_steps: int = 0       # steps known to have completed on the device
+    planned: int = 0          # steps queued
     detail: str = ""
 
     @property
@@ -57,9 +61,14 @@ class Request:
 
 
 class CudaBackend:
-    """The real engine: PyTorch device buffers + the library's C ABI."""
+    """The real engine: PyTorch device buffers + the library's C ABI.
 
-    def __init__(self, prec: str = "fp32", stream=None):
+    Each domain is created and initialised on a stream of its own, and the
+    batches step on the backend's stream; attach and detach only order the
+    two streams (no host wait), so a domain can be initialised, or read back
+    after it left the batch, while the next chunk of steps runs."""
+
+    def __init__(self, prec: str = "fp32", stream=None, autotune_steps: int = 0):
         import torch
 
         import paper_2205_00686_gb300 as lbm
@@ -69,6 +78,12 @@ class CudaBackend:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.batches: Dict[tuple, object] = {}
         self.handles: Dict[int, tuple] = {}
+        self.attached: Dict[int, bool] = {}
+        # with autotune_steps > 0, a batch's tile is chosen by
+        # lbm_batch_autotune (trials of that many steps on a shadow batch of
+        # its members' shapes) before its first chunk, and kept after
+        self.autotune_steps = int(autotune_steps)
+        self.tuned = set()
 
     def bytes_for(self, case) -> int:
         # state (both ping-pong copies) plus the field buffers read at retirement
@@ -80,9 +95,10 @@ class CudaBackend:
     def open(self, case):
         torch = self.torch
         nbytes = self.lbm.lbm_state_bytes(case.nx, case.ny, self.prec)
+        own = torch.cuda.Stream()
         buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         d = self.lbm.Domain(case.nx, case.ny, case.params, case.bc, prec=self.prec,
-                            stream=self.stream.cuda_stream, device_mem=buf.data_ptr(),
+                            stream=own.cuda_stream, device_mem=buf.data_ptr(),
                             device_bytes=nbytes)
         try:
             d.init_fields(*case.fields())
@@ -94,41 +110,68 @@ class CudaBackend:
         if key not in self.batches:
             self.batches[key] = self.lbm.Batch(stream=self.stream.cuda_stream)
         self.batches[key].attach(d)
-        h = (d, buf, key)
+        h = (d, buf, key, own)
         self.handles[id(h)] = h
+        self.attached[id(h)] = True
         return h
 
     def step(self, n: int):
-        for b in self.batches.values():
-            if len(b):
-                b.step(n)
+        """Queues n steps of every attached domain, then a copy of their error
+        words into pinned memory; returns a token for wait()."""
+        torch = self.torch
+        parts = []
+        for key, b in self.batches.items():
+            if not len(b):
+                continue
+            if self.autotune_steps and key not in self.tuned:
+                b.autotune(self.autotune_steps)
+                self.tuned.add(key)
+            b.step(n)
+            errs = torch.zeros(len(b), dtype=torch.int32).pin_memory()
+            b.errors_async(errs.data_ptr())
+            parts.append((errs, [id(self._handle_of(d)) for d in b.members]))
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        return ev, parts
 
-    def sync(self) -> Dict[int, int]:
-        """Waits; returns {id(handle): error} for handles with a device error."""
-        failed = False
-        for b in self.batches.values():
-            if len(b) and b.sync() != 0:
-                failed = True
-        errs = {}
-        if failed:
-            for hid, h in self.handles.items():
-                try:
-                    h[0].sync()
-                except self.lbm.LbmError as e:
-                    errs[hid] = e.code
-        return errs
+    def _handle_of(self, d):
+        for h in self.handles.values():
+            if h[0] is d:
+                return h
+        raise KeyError("domain without a handle")
 
-    def close(self, handle, read: bool = True):
-        d, buf, key = handle
-        self.handles.pop(id(handle), None)
-        self.batches[key].detach(d)
-        out = None
-        if read:
-            out = d.get_rho_u_T()
-        d.close()
-        del buf
+    def wait(self, token) -> Dict[int, int]:
+        """Waits for the chunk of `token` only; returns {id(handle): error}
+        for the domains whose error word was set by then."""
+        ev, parts = token
+        ev.synchronize()
+        out = {}
+        for errs, hids in parts:
+            for hid, e in zip(hids, errs.tolist()):
+                if e:
+                    out[hid] = self.lbm.LBM_ETIMEOUT if e & 4 else (
+                        self.lbm.LBM_EPSI if e & 1 else self.lbm.LBM_ENONFINITE)
         return out
 
+    def detach(self, handle):
+        if self.attached.get(id(handle)):
+            d, buf, key, own = handle
+            self.batches[key].detach(d)
+            self.attached[id(handle)] = False
+
+    def close(self, handle, read: bool = True):
+        self.detach(handle)
+        d, buf, key, own = handle
+        self.handles.pop(id(handle), None)
+        self.attached.pop(id(handle), None)
+        out = None
+        try:
+            if read:
+                out = d.get_rho_u_T()
+        finally:
+            d.close()
+            del buf
+        return out
 
 
 class Server:
@@ -148,6 +191,8 @@ class Server:
         self.t_start: Optional[float] = None
         self.max_active = 0
         self._next = 0
+        self.retiring = set()                    # rids whose steps are all queued
+        self._inflight = None                    # (token, [(rid, n)]) of the queued chunk
 
     # ---- request side -------------------------------------------------------
     def submit(self, case, steps: int, arrival: Optional[float] = None) -> Request:
@@ -202,34 +247,65 @@ class Server:
 
     def _retire(self, rid, error=0):
         r, h, need = self.active.pop(rid)
-        r.result = self.backend.close(h, read=error == 0)
+        self.retiring.discard(rid)
+        try:
+            r.result = self.backend.close(h, read=error == 0)
+        except Exception as e:      # a device error that surfaced at the read-back
+            r.result = None
+            error = error or getattr(e, "code", ADMIT_FAILED)
         r.error = error
         r.finished = self.clock()
         self.mem_used -= need
         self.finished.append(r)
 
     def tick(self) -> bool:
-        """One scheduling round: admit, advance a chunk, retire.  Returns
-        False when there is nothing left to do."""
+        """One scheduling round, pipelined so that the device always has a
+        chunk of steps queued while the host schedules:
+
+        1. domains whose steps are all queued leave the batch (stream-ordered);
+        2. waiting requests are admitted into the freed memory;
+        3. the next chunk of steps is queued for the domains still running;
+        4. the previous chunk is waited for (the new one keeps the device
+           busy) and its error words are checked: a failed domain is retired
+           at once, alone;
+        5. domains whose last step has completed are read back and retired.
+
+        Returns False when there is nothing left to do."""
         if self.t_start is None:
             self.t_start = self.clock()
+        for rid, (r, h, _) in self.active.items():
+            if r.planned >= r.steps and rid not in self.retiring:
+                self.backend.detach(h)
+                self.retiring.add(rid)
         self._admit()
-        if not self.active:
-            return bool(self.waiting)
-        # every active domain advances together: the chunk ends at the
-        # earliest completion so that no domain overshoots its target
-        n = min(self.chunk, min(r.steps - r.done_steps for r, _, _ in self.active.values()))
-        self.backend.step(n)
-        errs = self.backend.sync()
-        for rid, (r, h, _) in list(self.active.items()):
-            r.done_steps += n
-            self.node_updates += n * r.case.nx * r.case.ny
-            e = errs.get(id(h))
-            if e:
-                self._retire(rid, error=e)
-            elif r.done_steps >= r.steps:
+        running = [(rid, r) for rid, (r, _, _) in self.active.items() if rid not in self.retiring]
+        chunk = None
+        if running:
+            # every running domain advances together: the chunk ends at the
+            # earliest completion so that no domain overshoots its target
+            n = min(self.chunk, min(r.steps - r.planned for _, r in running))
+            token = self.backend.step(n)
+            for _, r in running:
+                r.planned += n
+            chunk = (token, [(rid, n) for rid, _ in running])
+        if self._inflight is not None:
+            token, members = self._inflight
+            errs = self.backend.wait(token)
+            for rid, n in members:
+                if rid not in self.active:        # cancelled meanwhile
+                    continue
+                r, h, _ = self.active[rid]
+                r.done_steps += n
+                self.node_updates += n * r.case.nx * r.case.ny
+                e = errs.get(id(h))
+                if e:
+                    self._retire(rid, error=e)
+        self._inflight = chunk
+        for rid in list(self.retiring):
+            r = self.active[rid][0]
+            if r.done_steps >= r.steps:
                 self._retire(rid)
-        return bool(self.active or self.waiting)
+        return bool(self.active or self.waiting or self._inflight is not None)
 
     def run(self, arrivals=None):
         """Runs until every request is done.  `arrivals` optionally lists

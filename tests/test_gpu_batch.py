@@ -322,3 +322,69 @@ def test_reconfigure_switches_buoyancy_on_with_the_last_mean_density():
     fe = P.field_errors(d.get_rho_u_T(), o.fields())
     assert max(fe.values()) <= 1e-12, fe
     d.close()
+
+
+def test_error_words_arrive_without_waiting_for_later_chunks():
+    """lbm_batch_errors_async queues a copy of each member's error word into
+    pinned host memory: after the event of the chunk it follows, the word of
+    the domain that left the EOS range is set and the others are clear, while
+    a later chunk may still be queued (it is not waited for)."""
+    import torch
+    import paper_2205_00686_gb300 as lbm
+    cases = mixed_cases()[:3]
+    stream = torch.cuda.Stream()
+    b = lbm.Batch(stream=stream.cuda_stream)
+    doms = []
+    for i, c in enumerate(cases):
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+        rho = c.rho.copy()
+        if i == 1:
+            rho[c.ny // 2, c.nx // 2] = 9.7       # psi^2 < 0 there
+        d.init_fields(rho, c.ux, c.uy, c.T)
+        b.attach(d)
+        doms.append(d)
+    errs = torch.full((3,), -1, dtype=torch.int32).pin_memory()
+    b.step(2)
+    b.errors_async(errs.data_ptr())
+    ev = torch.cuda.Event()
+    ev.record(stream)
+    b.step(40)                                   # queued behind, not waited for
+    ev.synchronize()
+    e = errs.tolist()
+    assert e[0] == 0 and e[2] == 0 and e[1] & 1, e
+    assert b.sync() == lbm.LBM_EPSI
+    b.close()
+    for d in doms:
+        d.close()
+
+
+def test_detached_domain_reads_back_after_its_last_batched_step():
+    """A domain detached while a later chunk of the batch is still queued
+    reads back the state its last batched step left (its own stream waits
+    for the batch's steps queued before the detach, and no longer), and
+    equals its solo run."""
+    import torch
+    import paper_2205_00686_gb300 as lbm
+    cases = mixed_cases()[:3]
+    bstream = torch.cuda.Stream()
+    b = lbm.Batch(stream=bstream.cuda_stream)
+    doms = []
+    for c in cases:
+        own = torch.cuda.Stream()
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32", stream=own.cuda_stream)
+        d.init_fields(*c.fields())
+        b.attach(d)
+        doms.append((d, own))
+    b.step(30)
+    b.detach(doms[0][0])
+    b.step(400)                                  # the others go on
+    f, g, _ = doms[0][0].populations()
+    fs, gs, _ = solo(cases[0], 30, "fp32")
+    assert np.array_equal(f, fs) and np.array_equal(g, gs)
+    assert b.sync() == 0
+    for (d, _), c in zip(doms[1:], cases[1:]):
+        b.detach(d)
+        f, g, _ = d.populations()
+        fs, gs, _ = solo(c, 430, "fp32")
+        assert np.array_equal(f, fs) and np.array_equal(g, gs), c.name
+    b.close()

@@ -16,6 +16,9 @@ class FakeCase:
 
 
 class FakeBackend:
+    """Steps attached handles at once; wait() reports the error words of a
+    chunk's members, as the device engine does one chunk later."""
+
     def __init__(self, fail_tags=(), fail_open_tags=()):
         self.open_handles = {}
         self.log = []
@@ -30,7 +33,7 @@ class FakeBackend:
     def open(self, case):
         if case.tag in self.fail_open_tags:
             raise MemoryError("device allocation failed")
-        h = {"case": case, "steps": 0}
+        h = {"case": case, "steps": 0, "attached": True}
         self.open_handles[id(h)] = h
         self._live_bytes += self.bytes_for(case)
         self.peak_bytes = max(self.peak_bytes, self._live_bytes)
@@ -38,12 +41,18 @@ class FakeBackend:
         return h
 
     def step(self, n):
-        for h in self.open_handles.values():
+        live = [h for h in self.open_handles.values() if h["attached"]]
+        for h in live:
             h["steps"] += n
-        self.log.append(("step", n, sorted(h["case"].tag for h in self.open_handles.values())))
+        self.log.append(("step", n, sorted(h["case"].tag for h in live)))
+        return [id(h) for h in live]
 
-    def sync(self):
-        return {k: -4 for k, h in self.open_handles.items() if h["case"].tag in self.fail_tags}
+    def wait(self, token):
+        return {k: -4 for k in token
+                if k in self.open_handles and self.open_handles[k]["case"].tag in self.fail_tags}
+
+    def detach(self, h):
+        h["attached"] = False
 
     def close(self, h, read=True):
         del self.open_handles[id(h)]
