@@ -202,6 +202,37 @@ int lbm_sync(lbm_ctx* ctx);
 int lbm_save(lbm_ctx* ctx, const char* path);
 int lbm_load(lbm_ctx* ctx, const char* path);
 
+/* One domain split into slabs of rows, one context per slab.  The paper
+ * has no counterpart (it runs one domain on one machine); these calls only
+ * move and combine state so that the split computes what one context of
+ * the whole domain computes.  A slab context holds its own rows plus halo
+ * rows copied from its neighbours before each step (three rows per step
+ * between exchanges: the step reads rows up to three away), its inner edges
+ * open with adiabatic temperature (they only shape halo rows, which are
+ * overwritten), and the same rho_ref / T_ref as the others (set in
+ * lbm_params), so that raw rows move between slabs unchanged.
+ *
+ * Bytes of n rows of every state plane, packed [plane][row][nx] (f 0..8, g
+ * 0..4, P^{n-1}; storage types of the context's precision). */
+size_t lbm_rows_bytes(const lbm_ctx* ctx, int n);
+/* Copies rows [y0, y0 + n) of the current state into / from a device buffer
+ * of lbm_rows_bytes(ctx, n) bytes in that layout, queued on the context
+ * stream (after its queued steps; no host wait).  LBM_EINVAL for rows outside
+ * [0, ny), LBM_ESTATE before lbm_init_fields or while attached to a batch. */
+int lbm_pack_rows(lbm_ctx* ctx, int y0, int n, void* dev_buf);
+int lbm_unpack_rows(lbm_ctx* ctx, int y0, int n, const void* dev_buf);
+/* Restricts the density sum behind rho_ave (Section 4.3) to the slab's own
+ * rows [own_y0, own_y1) and takes the mean over global_nodes nodes (the
+ * whole domain's count).  After each step the slabs' sums are to be added
+ * into the ring slot the step published (lbm_mass_ring) before the next
+ * step runs. */
+int lbm_set_partition(lbm_ctx* ctx, int own_y0, int own_y1, long long global_nodes);
+/* Device address of the context's three-slot density-sum ring (doubles):
+ * step s publishes sum rho of its rows into slot s % 3 and reads slot
+ * (s + 2) % 3 (the previous step's); lbm_init_fields sets slot 2 for step 0.
+ * The caller may overwrite a slot in stream order between steps. */
+int lbm_mass_ring(lbm_ctx* ctx, double** dev_ring);
+
 /* Frees the context (synchronising first).  NULL is accepted. */
 void lbm_destroy(lbm_ctx* ctx);
 

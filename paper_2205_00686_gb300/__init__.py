@@ -42,7 +42,8 @@ ABI_FUNCTIONS = (
     "lbm_batch_get_tile", "lbm_set_tile", "lbm_get_tile",
     "lbm_autotune", "lbm_set_staging", "lbm_get_staging", "lbm_set_wait_probe",
     "lbm_diag_reduce_noalloc", "lbm_reconfigure", "lbm_contact_angle",
-    "lbm_regions",
+    "lbm_regions", "lbm_rows_bytes", "lbm_pack_rows", "lbm_unpack_rows", "lbm_set_partition",
+    "lbm_mass_ring",
     # include/lbm3d.h
     "lbm3d_state_bytes", "lbm3d_create", "lbm3d_init_fields", "lbm3d_step", "lbm3d_get_fields",
     "lbm3d_get_populations", "lbm3d_diagnostics", "lbm3d_step_count", "lbm3d_sync",
@@ -150,6 +151,12 @@ def lib():
                                          ctypes.c_double, ctypes.c_double, _vp, _vp],
                                         ctypes.c_int),
             "lbm_reconfigure": ([_vp, P, B], ctypes.c_int),
+            "lbm_rows_bytes": ([_vp, ctypes.c_int], ctypes.c_size_t),
+            "lbm_pack_rows": ([_vp, ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
+            "lbm_unpack_rows": ([_vp, ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
+            "lbm_set_partition": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_longlong],
+                                  ctypes.c_int),
+            "lbm_mass_ring": ([_vp, ctypes.POINTER(_vp)], ctypes.c_int),
             "lbm_contact_angle": ([_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    ctypes.POINTER(lbm_contact)], ctypes.c_int),
             "lbm_regions": ([_vp, ctypes.c_double, ctypes.c_int, _vp,
@@ -334,6 +341,26 @@ class Domain:
     @property
     def last_error(self) -> str:
         return lib().lbm_last_error(self._h).decode()
+
+    # ---- slabs of one larger domain (lbm_rows_bytes ... lbm_mass_ring) ----
+    def rows_bytes(self, n: int) -> int:
+        return int(lib().lbm_rows_bytes(self._h, int(n)))
+
+    def pack_rows(self, y0: int, n: int, dev_ptr: int):
+        _check(lib().lbm_pack_rows(self._h, int(y0), int(n), ctypes.c_void_p(dev_ptr)), self._h)
+
+    def unpack_rows(self, y0: int, n: int, dev_ptr: int):
+        _check(lib().lbm_unpack_rows(self._h, int(y0), int(n), ctypes.c_void_p(dev_ptr)), self._h)
+
+    def set_partition(self, own_y0: int, own_y1: int, global_nodes: int):
+        _check(lib().lbm_set_partition(self._h, int(own_y0), int(own_y1), int(global_nodes)),
+               self._h)
+
+    def mass_ring(self) -> int:
+        """Device address of the three-slot density-sum ring (doubles)."""
+        p = _vp()
+        _check(lib().lbm_mass_ring(self._h, ctypes.byref(p)), self._h)
+        return int(p.value)
 
     def reconfigure(self, params: dict, bc: dict):
         """New params / boundary values for the following steps (flow boundary

@@ -464,6 +464,8 @@ int lbm_create(int nx, int ny, const lbm_params* params, const lbm_bc* bc, int p
     I.ctl = c->ctl;
     I.nx = nx;
     I.ny = ny;
+    I.own_y0 = 0;
+    I.own_y1 = ny;
     // the plane stride used by the kernels is ny * pitch elements: keep the
     // rounded plane sizes consistent with it
     I.pitch = c->lay.pitch;
@@ -704,6 +706,66 @@ struct CkptHeader {
 
 static size_t ckpt_payload(const lbm_ctx* c) {
     return 9 * c->lay.planeF + 5 * c->lay.planeG + c->lay.planeP;
+}
+
+// ---------------------------------------------------------------------------
+// one domain split into slabs of rows: halo rows between slabs and the
+// combined density sum behind rho_ave
+
+size_t lbm_rows_bytes(const lbm_ctx* c, int n) {
+    if (!c || n < 0) return 0;
+    return (size_t)n * c->nx * (9 * elem_f(c->prec) + 5 * elem_g(c->prec) + elem_P(c->prec));
+}
+
+// copies rows [y0, y0 + n) of every state plane (f 0..8, g 0..4, P) between
+// the current state and a packed buffer [plane][row][nx], on the ctx stream
+static int rows_copy(lbm_ctx* c, int y0, int n, void* buf, bool pack) {
+    if (!c || !buf || n < 0 || y0 < 0 || y0 + n > c->ny) return LBM_EINVAL;
+    if (!c->initialized) return set_err(c, LBM_ESTATE, "no state yet");
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    if (n == 0) return LBM_OK;
+    const int par = (int)(c->step & 1);
+    const size_t ef = elem_f(c->prec), eg = elem_g(c->prec), ep = elem_P(c->prec);
+    char* b = (char*)buf;
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 15 && e == cudaSuccess; ++q) {
+        const size_t es = q < 9 ? ef : (q < 14 ? eg : ep);
+        char* plane = q < 9 ? (char*)c->inst.f[par] + q * c->lay.planeF
+                            : (q < 14 ? (char*)c->inst.g[par] + (q - 9) * c->lay.planeG
+                                      : (char*)c->inst.P[par]);
+        char* rows = plane + (size_t)y0 * c->lay.pitch * es;
+        const size_t spitch = (size_t)c->lay.pitch * es, w = (size_t)c->nx * es;
+        if (pack)
+            e = cudaMemcpy2DAsync(b, w, rows, spitch, w, n, cudaMemcpyDeviceToDevice, c->stream);
+        else
+            e = cudaMemcpy2DAsync(rows, spitch, b, w, w, n, cudaMemcpyDeviceToDevice, c->stream);
+        b += w * n;
+    }
+    return cuda_err(c, e, pack ? "lbm_pack_rows" : "lbm_unpack_rows");
+}
+
+int lbm_pack_rows(lbm_ctx* c, int y0, int n, void* dev_buf) { return rows_copy(c, y0, n, dev_buf, true); }
+
+int lbm_unpack_rows(lbm_ctx* c, int y0, int n, const void* dev_buf) {
+    return rows_copy(c, y0, n, const_cast<void*>(dev_buf), false);
+}
+
+int lbm_set_partition(lbm_ctx* c, int own_y0, int own_y1, long long global_nodes) {
+    if (!c || own_y0 < 0 || own_y1 > c->ny || own_y0 >= own_y1 ||
+        global_nodes < (long long)c->nx * (own_y1 - own_y0))
+        return LBM_EINVAL;
+    if (c->batch) return set_err(c, LBM_ESTATE, "context is attached to a batch");
+    c->inst.own_y0 = own_y0;
+    c->inst.own_y1 = own_y1;
+    c->inst.inv_n = 1.0 / (double)global_nodes;
+    drop_graph(&c->graph);
+    return ctx_upload_inst(c);
+}
+
+int lbm_mass_ring(lbm_ctx* c, double** dev_ring) {
+    if (!c || !dev_ring) return LBM_EINVAL;
+    *dev_ring = c->ctl->mass;
+    return LBM_OK;
 }
 
 int lbm_save(lbm_ctx* c, const char* path) {

@@ -63,6 +63,10 @@ struct Inst {
     int heater_x0, heater_x1;
     double T_edge[4], T_heater, cot_theta;
     double rho_ref, T_ref, inv_n;
+    // rows [own_y0, own_y1) enter the density sum behind rho_ave; inv_n is
+    // 1 / (nodes the mean is taken over).  The whole domain unless it is one
+    // slab of a larger domain (lbm_set_partition).
+    int own_y0, own_y1;
 };
 
 // A work unit of the fused step: output columns [x0, x1), rows [y0, y1) of

@@ -211,7 +211,7 @@ struct Sweep {
     const Phys<R>& P;
     SM& S;
     WallRings<R, NT>& WR;   // valid only for domains with walls
-    int t, nx, ny, pitch, y0, y1;
+    int t, nx, ny, pitch, y0, y1, my0, my1;
     bool perx, pery, tperx, tpery, first, use_mass, wallS, wallN;
     unsigned plane;
     const TF* __restrict__ fsrc;
@@ -262,6 +262,9 @@ struct Sweep {
         pitch = I.pitch;
         y0 = U.y0;
         y1 = U.y1;
+        // rows of this unit that enter the density sum (a slab's own rows)
+        my0 = max(y0, I.own_y0);
+        my1 = min(y1, I.own_y1);
         const int x0 = U.x0, x1 = U.x1;
         perx = I.flow[EW] == PERIODIC;
         pery = I.flow[ES] == PERIODIC;
@@ -747,7 +750,7 @@ struct Sweep {
             }
             // this unit's output rows only (steady iterations also load the
             // three rows above the segment)
-            mass_acc += (inD && k >= y0 && k < y1) ? rho_a : R(0);
+            mass_acc += (inD && k >= my0 && k < my1) ? rho_a : R(0);
         }
         __syncthreads();
 
