@@ -287,6 +287,7 @@ def served_check(n_inst, steps, budget_gb=1.0):
     solo_mlups = sum(c.nx * c.ny for c in cases[:m]) * steps / t_solo / 1e6
     return {"instances": n_inst, "steps_each": steps, "total_nodes": nodes,
             "budget_gb": budget_gb, "mlups": round(st["mlups"], 1),
+            "mlups_at_capacity": round(st["mlups_at_capacity"], 1) if st["mlups_at_capacity"] else None,
             "p50_s": round(st["p50_s"], 4), "p99_s": round(st["p99_s"], 4),
             "wall_s": round(st["wall_s"], 2), "failed": st["failed"],
             "max_concurrent": st["max_active"],

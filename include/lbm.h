@@ -185,6 +185,15 @@ int lbm_get_populations(lbm_ctx* ctx, double* f, double* g, double* P);
 int lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g, const double* P,
                         long long step, double rho_ave_prev);
 
+/* Makes the context stop at step count `target` (> 0; 0 removes the stop):
+ * the launches of lbm_step or lbm_batch_step leave a context that has
+ * reached it untouched (state, step counter, buoyancy history), so domains
+ * with different step counts can share chunks of batched launches and each
+ * end exactly at its own.  Ordered with the steps on the stream that runs
+ * them (the batch's while attached).  lbm_init_fields, lbm_set_populations
+ * and lbm_load remove the stop.  The paper has no counterpart. */
+int lbm_set_target(lbm_ctx* ctx, long long target);
+
 /* Number of completed steps. */
 long long lbm_step_count(const lbm_ctx* ctx);
 

@@ -36,6 +36,7 @@ ABI_FUNCTIONS = (
     "lbm_default_params", "lbm_state_bytes", "lbm_create", "lbm_init_fields", "lbm_step",
     "lbm_get_rho_u_T", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
     "lbm_step_count", "lbm_sync", "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error",
+    "lbm_set_target",
     "lbm_batch_create", "lbm_batch_attach", "lbm_batch_detach", "lbm_batch_size",
     "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy", "lbm_batch_autotune",
     "lbm_batch_errors_async",
@@ -124,6 +125,7 @@ def lib():
             "lbm_set_populations": ([_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_double],
                                     ctypes.c_int),
             "lbm_step_count": ([_vp], ctypes.c_longlong),
+            "lbm_set_target": ([_vp, ctypes.c_longlong], ctypes.c_int),
             "lbm_sync": ([_vp], ctypes.c_int),
             "lbm_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
             "lbm_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
@@ -341,6 +343,10 @@ class Domain:
     @property
     def last_error(self) -> str:
         return lib().lbm_last_error(self._h).decode()
+
+    def set_target(self, target: int):
+        """Stop at step count `target` (0: no stop); see lbm_set_target."""
+        _check(lib().lbm_set_target(self._h, int(target)), self._h)
 
     # ---- slabs of one larger domain (lbm_rows_bytes ... lbm_mass_ring) ----
     def rows_bytes(self, n: int) -> int:

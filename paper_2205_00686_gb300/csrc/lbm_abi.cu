@@ -215,6 +215,7 @@ struct lbm_ctx {
     int n_units = 0, grid = 1, threads = 128, rows = 64, staged = 0, wait_probe = 0;
     cudaGraphExec_t graph = nullptr;
     long long step = 0;
+    long long target = 0;      // the step the domain stops at (0: none), as on the device
     bool initialized = false;
     int sticky = LBM_OK;
     std::string err;
@@ -549,9 +550,30 @@ int lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, const doubl
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_err(c, e, "lbm_init_fields");
     c->step = 0;
+    c->target = 0;
     c->sticky = LBM_OK;
     c->initialized = true;
     c->err.clear();
+    return LBM_OK;
+}
+
+// the step count after n more launches: a domain stops at its target
+static long long step_after(const lbm_ctx* c, int n) {
+    const long long s = c->step + n;
+    return c->target > 0 ? std::min(s, std::max(c->step, c->target)) : s;
+}
+
+__global__ void k_set_target(Ctl* ctl, long long target) { ctl->target = target; }
+
+int lbm_set_target(lbm_ctx* c, long long target) {
+    if (!c || target < 0) return LBM_EINVAL;
+    if (!c->initialized) return set_err(c, LBM_ESTATE, "lbm_set_target before lbm_init_fields");
+    // in stream order with the steps that read it: the batch's stream while
+    // the context is attached
+    k_set_target<<<1, 1, 0, c->batch ? c->batch->stream : c->stream>>>(c->ctl, target);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(c, e, "lbm_set_target");
+    c->target = target;
     return LBM_OK;
 }
 
@@ -562,7 +584,7 @@ int lbm_step(lbm_ctx* c, int n) {
     if (c->sticky) return c->sticky;
     if (n == 0) return LBM_OK;
     int rc = enqueue_steps(c->stream, &c->graph, ctx_launch(c), c->prec, c->threads, n, c);
-    if (rc == LBM_OK) c->step += n;
+    if (rc == LBM_OK) c->step = step_after(c, n);
     return rc;
 }
 
@@ -683,6 +705,7 @@ int lbm_set_populations(lbm_ctx* c, const double* f, const double* g, const doub
     cudaFree(buf);
     if (rc) return rc;
     c->step = step;
+    c->target = 0;
     c->sticky = LBM_OK;
     c->initialized = true;
     c->err.clear();
@@ -847,6 +870,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
     if (e == cudaSuccess) e = cudaMemcpy(c->inst_dev, &c->inst, sizeof(Inst), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_err(c, e, "lbm_load");
     c->step = hd.step;
+    c->target = 0;
     c->sticky = LBM_OK;
     c->initialized = true;
     c->err.clear();
@@ -1330,7 +1354,7 @@ int lbm_batch_step(lbm_batch* b, int n) {
     L.phys = b->phys;
     int rc = enqueue_steps(b->stream, &b->graph, L, b->prec, b->threads, n, b->members[0]);
     if (rc == LBM_OK)
-        for (lbm_ctx* c : b->members) c->step += n;
+        for (lbm_ctx* c : b->members) c->step = step_after(c, n);
     return rc;
 }
 

@@ -29,9 +29,18 @@ struct Ctl {
     long long step;
     double mass[3];
     long long massq[3];
+    // the step count at which the domain stops (> 0), or 0 for none: a
+    // launch skips the units of a domain that has reached it, so its state,
+    // step counter and density ring stay as they are
+    long long target;
     int err;
     int pad;
 };
+
+__device__ __forceinline__ bool ctl_stopped(const Ctl* c) {
+    const long long tg = __ldcg(&c->target);
+    return tg > 0 && __ldcg(&c->step) >= tg;
+}
 
 // fixed-point scale of Ctl::massq for a domain of N = 1 / inv_n nodes:
 // 2^(58 - e) with N < 2^e.  Densities stay below 16 (the EOS ends at 1/b =

@@ -92,7 +92,7 @@ class CudaBackend:
     def _key(self, case):
         return tuple(sorted((k, float(v)) for k, v in case.params.items()))
 
-    def open(self, case):
+    def open(self, case, steps: int):
         torch = self.torch
         nbytes = self.lbm.lbm_state_bytes(case.nx, case.ny, self.prec)
         own = torch.cuda.Stream()
@@ -102,6 +102,8 @@ class CudaBackend:
                             device_bytes=nbytes)
         try:
             d.init_fields(*case.fields())
+            # the domain stops at its own step count inside shared chunks
+            d.set_target(int(steps))
         except Exception:
             d.close()
             del buf
@@ -192,7 +194,13 @@ class Server:
         self.max_active = 0
         self._next = 0
         self.retiring = set()                    # rids whose steps are all queued
-        self._inflight = None                    # (token, [(rid, n)]) of the queued chunk
+        self._inflight = None                    # (token, [(rid, n)], at capacity) of the queued chunk
+        # chunks queued while requests were still waiting for memory (the
+        # device holds as much as the budget allows): their node updates and
+        # the time from the previous chunk's completion to theirs
+        self._cap_nodes = 0
+        self._cap_time = 0.0
+        self._last_done = None
 
     # ---- request side -------------------------------------------------------
     def submit(self, case, steps: int, arrival: Optional[float] = None) -> Request:
@@ -217,7 +225,7 @@ class Server:
                 break
             self.waiting.popleft()
             try:
-                h = self.backend.open(r.case)
+                h = self.backend.open(r.case, r.steps)
             except Exception as e:      # allocation or creation failed: this request only
                 r.admitted = r.finished = self.clock()
                 r.error = ADMIT_FAILED
@@ -281,25 +289,36 @@ class Server:
         running = [(rid, r) for rid, (r, _, _) in self.active.items() if rid not in self.retiring]
         chunk = None
         if running:
-            # every running domain advances together: the chunk ends at the
-            # earliest completion so that no domain overshoots its target
-            n = min(self.chunk, min(r.steps - r.planned for _, r in running))
+            # every running domain advances together by a full chunk; each
+            # stops at its own step count inside it (the library's per-domain
+            # target), so no domain overshoots and no chunk is cut short
+            n = self.chunk
             token = self.backend.step(n)
-            for _, r in running:
-                r.planned += n
-            chunk = (token, [(rid, n) for rid, _ in running])
+            moved = []
+            for rid, r in running:
+                k = min(n, r.steps - r.planned)
+                r.planned += k
+                moved.append((rid, k))
+            chunk = (token, moved, bool(self.waiting))
         if self._inflight is not None:
-            token, members = self._inflight
+            token, members, at_cap = self._inflight
             errs = self.backend.wait(token)
+            now = self.clock()
+            nodes = 0
             for rid, n in members:
                 if rid not in self.active:        # cancelled meanwhile
                     continue
                 r, h, _ = self.active[rid]
                 r.done_steps += n
+                nodes += n * r.case.nx * r.case.ny
                 self.node_updates += n * r.case.nx * r.case.ny
                 e = errs.get(id(h))
                 if e:
                     self._retire(rid, error=e)
+            if at_cap and self._last_done is not None:
+                self._cap_nodes += nodes
+                self._cap_time += now - self._last_done
+            self._last_done = now
         self._inflight = chunk
         for rid in list(self.retiring):
             r = self.active[rid][0]
@@ -342,5 +361,7 @@ class Server:
             "node_updates": int(self.node_updates),
             "wall_s": wall,
             "mlups": self.node_updates / wall / 1e6 if wall > 0 else None,
+            # while requests waited for memory: the device as full as the budget allows
+            "mlups_at_capacity": self._cap_nodes / self._cap_time / 1e6 if self._cap_time > 0 else None,
             "max_active": self.max_active,
         }

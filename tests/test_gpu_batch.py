@@ -388,3 +388,39 @@ def test_detached_domain_reads_back_after_its_last_batched_step():
         fs, gs, _ = solo(c, 430, "fp32")
         assert np.array_equal(f, fs) and np.array_equal(g, gs), c.name
     b.close()
+
+
+def test_domains_stop_at_their_own_targets_inside_shared_launches():
+    """lbm_set_target: in a batch stepped 100 times, a domain with target 30
+    and one with target 70 end exactly at those step counts with their solo
+    states, buoyancy history included, while a third runs all 100; a solo
+    domain stops the same way and continues once the target is lifted."""
+    import paper_2205_00686_gb300 as lbm
+    cases = mixed_cases(gravity=2e-5)[:3]
+    b = lbm.Batch()
+    doms = []
+    for c, tgt in zip(cases, (30, 70, 0)):
+        d = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+        d.init_fields(*c.fields())
+        d.set_target(tgt)
+        b.attach(d)
+        doms.append(d)
+    threads, rows, staged = b.tile()
+    b.step(100)
+    assert b.sync() == 0
+    for d, c, n in zip(doms, cases, (30, 70, 100)):
+        b.detach(d)
+        assert d.step_count == n
+        s = lbm.Domain(c.nx, c.ny, c.params, c.bc, prec="fp32")
+        s.set_tile(threads, rows)
+        s.staged = staged
+        s.init_fields(*c.fields())
+        s.step(n)
+        for a, r in zip(d.populations(), s.populations()):
+            assert np.array_equal(a, r), (c.name, n)
+        s.close()
+    d = doms[0]
+    d.set_target(0)
+    d.step(5)
+    assert d.step_count == 35
+    b.close()

@@ -30,10 +30,10 @@ class FakeBackend:
     def bytes_for(self, case):
         return case.nx * case.ny * 100
 
-    def open(self, case):
+    def open(self, case, steps):
         if case.tag in self.fail_open_tags:
             raise MemoryError("device allocation failed")
-        h = {"case": case, "steps": 0, "attached": True}
+        h = {"case": case, "steps": 0, "target": steps, "attached": True}
         self.open_handles[id(h)] = h
         self._live_bytes += self.bytes_for(case)
         self.peak_bytes = max(self.peak_bytes, self._live_bytes)
@@ -43,7 +43,7 @@ class FakeBackend:
     def step(self, n):
         live = [h for h in self.open_handles.values() if h["attached"]]
         for h in live:
-            h["steps"] += n
+            h["steps"] = min(h["steps"] + n, h["target"])
         self.log.append(("step", n, sorted(h["case"].tag for h in live)))
         return [id(h) for h in live]
 
