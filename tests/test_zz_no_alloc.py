@@ -63,3 +63,39 @@ def test_noalloc_rejects_sizes_beyond_its_capacity():
     assert rc == lbm.LBM_OK
     torch.cuda.synchronize()
     assert float(buf[:7].abs().sum()) == 0.0
+
+
+def test_noalloc_at_capacity_and_allocates_nothing():
+    """At the largest accepted size (LBM_NOALLOC_MAX_NODES nodes, every one of
+    the 4096 blocks of the fixed array in use) the sums equal a plain PyTorch
+    FP64 reduction of the same fields; and a call after the first one leaves
+    the device's free memory exactly as it was: nothing is allocated."""
+    import torch
+
+    import paper_2205_00686_gb300 as lbm
+    n = lbm.LBM_NOALLOC_MAX_NODES
+    g = torch.Generator(device="cuda").manual_seed(5)
+    rho = 0.38 + 6.2 * torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+    ux = 0.02 * (torch.rand(n, dtype=torch.float64, device="cuda", generator=g) - 0.5)
+    uy = 0.02 * (torch.rand(n, dtype=torch.float64, device="cuda", generator=g) - 0.5)
+    T = 0.09 + 0.01 * torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+    cv, rl, rg = 5.0, 6.5, 0.38
+    out = torch.empty(7, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    args = [rho.data_ptr(), ux.data_ptr(), uy.data_ptr(), T.data_ptr(), n, cv, rl, rg,
+            out.data_ptr(), stream.cuda_stream]
+    assert lbm.lbm_diag_reduce_noalloc(*args) == lbm.LBM_OK
+    torch.cuda.synchronize()
+    first = out.clone()
+    free0 = torch.cuda.mem_get_info()[0]
+    out.fill_(-1.0)
+    assert lbm.lbm_diag_reduce_noalloc(*args) == lbm.LBM_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.equal(out, first)
+    mid = 0.5 * (rl + rg)
+    liq = rho > mid
+    ref = [rho.sum(), (rho * cv * T).sum(), rho[liq].sum(), liq.sum().double(),
+           ((rho - rg) / (rl - rg)).clamp(0, 1).sum(), torch.sqrt(ux * ux + uy * uy).max(), 0.0]
+    for k, (a, b) in enumerate(zip(out.tolist(), [float(r) for r in ref])):
+        assert abs(a - b) <= 1e-12 * max(1.0, abs(b)), (k, a, b)
