@@ -319,6 +319,7 @@ static StepLaunch ctx_launch(const lbm_ctx* c) {
     L.walls = has_walls(c->inst) ? 1 : 0;
     L.staged = c->staged;
     L.wait_probe = c->wait_probe;
+    L.targets = c->target > 0 ? 1 : 0;
     L.phys = c->phys;
     return L;
 }
@@ -573,6 +574,12 @@ int lbm_set_target(lbm_ctx* c, long long target) {
     k_set_target<<<1, 1, 0, c->batch ? c->batch->stream : c->stream>>>(c->ctl, target);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(c, e, "lbm_set_target");
+    // the launches carry whether any domain has a target: captured graphs
+    // are rebuilt when that can change
+    if ((c->target > 0) != (target > 0)) {
+        drop_graph(&c->graph);
+        if (c->batch) drop_graph(&c->batch->graph);
+    }
     c->target = target;
     return LBM_OK;
 }
@@ -1351,6 +1358,8 @@ int lbm_batch_step(lbm_batch* b, int n) {
     L.walls = b->walls;
     L.staged = b->staged;
     L.wait_probe = 0;
+    L.targets = 0;
+    for (lbm_ctx* c : b->members) L.targets |= c->target > 0 ? 1 : 0;
     L.phys = b->phys;
     int rc = enqueue_steps(b->stream, &b->graph, L, b->prec, b->threads, n, b->members[0]);
     if (rc == LBM_OK)

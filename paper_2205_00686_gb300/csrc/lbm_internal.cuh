@@ -268,6 +268,7 @@ struct StepLaunch {
     int walls;         // some domain has a wall: the launch carries the wall rings
     int staged;        // FP32 / FP16-g: rows arrive by bulk copies (stage_eligible)
     int wait_probe;    // test hook: staged CTAs also wait on an mbarrier nothing arms
+    int targets;       // some domain has a target step (lbm_set_target)
     PhysD phys;
 };
 

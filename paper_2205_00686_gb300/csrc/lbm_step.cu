@@ -1071,8 +1071,9 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
         if (u >= L.n_units) break;
         const Unit U = L.units[u];
         // a domain at its target step sits this launch out (every thread
-        // reads the same control block, so the branch is uniform)
-        if (ctl_stopped(L.insts[U.inst].ctl)) continue;
+        // reads the same control block, so the branch is uniform); launches
+        // without targets skip the check and its loads
+        if (L.targets && ctl_stopped(L.insts[U.inst].ctl)) continue;
         process_unit<PREC, NT, UNIT, STG>(L.insts[U.inst], U, P, S, WR, mph, L.wait_probe);
     }
     // the last CTA to finish (its thread 0 finds the finished-CTA count at
@@ -1091,7 +1092,7 @@ __global__ void __launch_bounds__(NT, (PREC == 0) ? 1 : (512 / NT))
         __threadfence();
         for (int i = threadIdx.x; i < L.n_inst; i += NT) {
             Ctl* c = L.insts[i].ctl;
-            if (ctl_stopped(c)) continue;
+            if (L.targets && ctl_stopped(c)) continue;
             const long long s = __ldcg(&c->step);
             c->mass[s % 3] = massq_value(__ldcg(&c->massq[s % 3]), massq_scale(L.insts[i].inv_n));
             c->massq[(s + 1) % 3] = 0;
