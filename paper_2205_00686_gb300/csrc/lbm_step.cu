@@ -228,6 +228,9 @@ struct Sweep {
     R twW2, twE2, twS2, twN2;
     // carried from A(k-1) to B(k-1), and the next row's loads
     R fp[9], rhop, rhodp, jxp, jyp, psip, irp;
+    // unit rates: of a row's populations stage B needs besides rho and j only
+    // the stress moments m_7 and m_8, formed in stage A (fp is then unused)
+    R m7p, m8p;
     R fa[9], ga[5], pa;
     R mass_acc;
     int errbits;
@@ -335,6 +338,7 @@ struct Sweep {
 
 #pragma unroll
         for (int q = 0; q < 9; ++q) fp[q] = R(0);
+        m7p = m8p = R(0);
         rhop = R(1);
         rhodp = jxp = jyp = psip = R(0);
         irp = R(1);
@@ -629,8 +633,14 @@ struct Sweep {
                 const bool bS = !vd && wallS, bN = !vu && wallN;
                 R fo[9];
                 if (P.frozen_flow) {
+                    if constexpr (UNIT) {
+                        const TF* fr = fsrc + (size_t)(pery ? wrapi(r, ny) : r) * pitch + gxl;
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) fo[q] = S.fs[a0][q][t];
+                        for (int q = 0; q < 9; ++q) fo[q] = (R)ld_st(fr + q * plane);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) fo[q] = S.fs[a0][q][t];
+                    }
                 } else {
                     fo[0] = S.fs[a0][0][t];
                     fo[1] = S.fs[a0][1][xl1];
@@ -705,6 +715,7 @@ struct Sweep {
             mph ^= 1u << fk;
         }
         R rho_a = R(1), rhod_a = R(0), jx_a = R(0), jy_a = R(0), psi_a = R(0), ir_a = R(1);
+        R m7_a = R(0), m8_a = R(0);
         if constexpr (STG) {
             if (doA && (STEADY || colvalid)) {
                 const R* fr = &S.fR[NF == 3 ? a0 : fq][0][sidx];
@@ -726,6 +737,10 @@ struct Sweep {
             const R T_a = Td + T_ref;
             jx_a = (fa[1] - fa[3]) + (fa[5] - fa[6]) + (fa[8] - fa[7]);
             jy_a = (fa[2] - fa[4]) + (fa[5] + fa[6]) - (fa[7] + fa[8]);
+            if constexpr (UNIT) {
+                m7_a = (fa[1] + fa[3]) - (fa[2] + fa[4]);
+                m8_a = (fa[5] + fa[7]) - (fa[6] + fa[8]);
+            }
             R q2, TdpdT;
             eos_node(P, rho_a, T_a, &q2, &TdpdT);
             if (colvalid && !(q2 >= R(0))) errbits |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
@@ -757,8 +772,10 @@ struct Sweep {
         // ================= phase beta =================
         // keep row k's populations for B(k) and issue the loads of row k + 1
         R fpn[9];
+        if constexpr (!UNIT) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) fpn[q] = fa[q];
+            for (int q = 0; q < 9; ++q) fpn[q] = fa[q];
+        }
         if constexpr (!STG) load_row(k + 1, kwn);
         // staged form: every thread is past its wait for row k, so row k's
         // mbarrier (and f slot) can take row k + 3
@@ -817,20 +834,23 @@ struct Sweep {
                 if (STEADY || (r >= y0 - 1 && r < y1 + 1 && inC)) {
                     R* fsw = &S.fs[a1][0][t];
                     if (P.frozen_flow) {
+                        // the populations stay as they are: stage D9 copies
+                        // them from the source state (unit rates), or from here
+                        if constexpr (!UNIT) {
 #pragma unroll
-                        for (int q = 0; q < 9; ++q) fsw[q * NT] = fp[q];
+                            for (int q = 0; q < 9; ++q) fsw[q * NT] = fp[q];
+                        }
                     } else if (UNIT) {
                         // s_e = s_eps = s_q = 1: those moments leave the
                         // collision at m^eq + F/2, so f* = M^{-1} m* needs of f
                         // only rho, j and the stresses m_7, m_8 (Eqs. 5, 7, 8)
-                        const R* f = fp;
                         const R rr = rhop;
                         const R rux = rr * ux, ruy = rr * uy;
                         const R ruu = rux * ux + ruy * uy;
                         const R uF = ux * Fx + uy * Fy;
                         const R Fm2 = P.negG * P.negG * (sx * sx + sy * sy);
-                        const R m7 = (f[1] + f[3]) - (f[2] + f[4]);
-                        const R m8 = (f[5] + f[7]) - (f[6] + f[8]);
+                        const R m7 = m7p;
+                        const R m8 = m8p;
                         const R F7 = R(2) * (ux * Fx - uy * Fy);
                         const R F8 = ux * Fy + uy * Fx;
                         // deviation-form m*_e, m*_eps (storage shifts them by
@@ -839,8 +859,7 @@ struct Sweep {
                         const R m2s = rhodp - R(3) * (ruu + uF) - R(0.5) * P.sig_eps * Fm2;
                         const R b0 = rhodp * R(1.0 / 9.0);
                         const R b1 = m1s * R(1.0 / 36.0), b2 = m2s * R(1.0 / 36.0);
-                        const R b7 = ((f[1] + f[3]) - (f[2] + f[4]) -
-                                      P.s_p * (m7 - (rux * ux - ruy * uy)) + P.hs_p * F7) * R(0.25);
+                        const R b7 = (m7 - P.s_p * (m7 - (rux * ux - ruy * uy)) + P.hs_p * F7) * R(0.25);
                         const R b8 = (m8 - P.s_p * (m8 - rux * uy) + P.hs_p * F8) * R(0.25);
                         // j* = j + F; q* = -(j + F) / 1 -> combined axis / diagonal terms
                         const R jxs = jxp + Fx, jys = jyp + Fy;
@@ -954,8 +973,13 @@ struct Sweep {
         }
         __syncthreads();
 
+        if constexpr (!UNIT) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) fp[q] = fpn[q];
+            for (int q = 0; q < 9; ++q) fp[q] = fpn[q];
+        } else {
+            m7p = m7_a;
+            m8p = m8_a;
+        }
         rhop = rho_a;
         rhodp = rhod_a;
         jxp = jx_a;
