@@ -197,6 +197,25 @@ __device__ __forceinline__ float f_sqrt(float x) {
 }
 __device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
 
+// Two-lane arithmetic.  In float it maps to Blackwell's paired FP32
+// instructions (one FADD2 / FMUL2 / FFMA2 does the work of two), each lane
+// rounded as the scalar operation; in double it is componentwise.  Subtraction
+// is a fused multiply-add with -1, which is exact in the product.
+__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 pr(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
 // Peng-Robinson pressure (Eq. 10) and psi^2 = 2 (p_EOS - rho/3) / G.
 template <class R>
 __device__ __forceinline__ R eos_p(const Phys<R>& P, R rho, R T) {

@@ -530,14 +530,17 @@ struct Sweep {
                     g0 = o0.x; g1 = o0.y; g2 = o0.z; g3 = o0.w; g4 = o1.x;
                     rho = o1.y; Pp = o1.z; TdpdT = o1.w;
                 }
-                const R Td = ((g0 + g1) + (g2 + g3)) + g4;
-                const R m1 = g1 - g3;
-                const R m2 = g2 - g4;
-                const R m3d = (g1 + g3) + (g2 + g4);
-                const R m4 = (g1 + g3) - (g2 + g4);
+                // (m_1, m_2) = (g1 - g3, g2 - g4) and the pair sums (g1 + g3, g2 + g4)
+                const R2 m12 = psub(pr(g1, g2), pr(g3, g4));
+                const R2 p13 = padd(pr(g1, g2), pr(g3, g4));
+                const R m1 = m12.x, m2 = m12.y;
+                const R Td = (g0 + p13.x) + p13.y;
+                const R m3d = p13.x + p13.y;
+                const R m4 = p13.x - p13.y;
                 // Eqs. 49-50: c_s^2 d_x T = -varsigma_1 m_1^(1), m_1^eq = 0
-                const R dTx = -P.vs1_cs2h * m1;
-                const R dTy = -P.vs1_cs2h * m2;
+                const R2 dT = pmul(pr(-P.vs1_cs2h, -P.vs1_cs2h), m12);
+                const R dTx = dT.x;
+                const R dTy = dT.y;
                 // neighbour rows: solid -> u = 0, open -> the boundary row
                 const bool vd = STEADY || pery || r - 1 >= 0, vu = STEADY || pery || r + 1 < ny;
                 const R2 uc = S.u[a0][t];
@@ -567,7 +570,9 @@ struct Sweep {
                 const R Pn = Q * f_rcp(rho) * P.inv_cv;
                 const R Qs = first ? Q : Q + R(0.5) * (Q - C * Pp);
                 // moment-space collision (Eqs. 39, 40, 47), deviation form
-                const R h1 = R(0.5) * P.one_m_vs1 * m1, h2 = R(0.5) * P.one_m_vs1 * m2;
+                const R hc = R(0.5) * P.one_m_vs1;
+                const R2 h12 = pmul(pr(hc, hc), m12);
+                const R h1 = h12.x, h2 = h12.y;
                 R gs0, gs1, gs2, gs3, gs4;
                 if (UNIT) {
                     // varsigma_3 = varsigma_4 = 1: m3* = w_dot (T + Qs), m4* = 0
@@ -576,10 +581,11 @@ struct Sweep {
                     // unfused: stage D5 subtracts g_0 from g*_0, and the
                     // staged form hands g*_0 over in a register
                     gs0 = mul_rn(P.w5_0, TQ);
-                    gs1 = a + h1;
-                    gs2 = a + h2;
-                    gs3 = a - h1;
-                    gs4 = a - h2;
+                    const R2 g12 = padd(pr(a, a), h12), g34 = psub(pr(a, a), h12);
+                    gs1 = g12.x;
+                    gs2 = g12.y;
+                    gs3 = g34.x;
+                    gs4 = g34.y;
                 } else {
                     const R m0s = Td + Qs;
                     const R m3s = m3d - P.vs3 * (m3d - P.w_dot * Td) + P.w_dot * Qs;
@@ -685,10 +691,15 @@ struct Sweep {
                     const R A4 = vu ? cgs4 : (dirN ? twN2 - dgs2 : dgs2);
                     const R iC = f_rcp(drho * P.cv);
                     go[0] = dg[0] + (dgs0 - dg[0]) * iC;
-                    go[1] = dg[1] + (A1 - dg[1]) * iC;
-                    go[2] = dg[2] + (A2 - dg[2]) * iC;
-                    go[3] = dg[3] + (A3 - dg[3]) * iC;
-                    go[4] = dg[4] + (A4 - dg[4]) * iC;
+                    // g_i + (A_i - g_i) / (rho c_v) for (1, 3) and (2, 4) in pairs
+                    const R2 iC2 = pr(iC, iC);
+                    const R2 g13 = pr(dg[1], dg[3]), g24 = pr(dg[2], dg[4]);
+                    const R2 o13 = pfma(psub(pr(A1, A3), g13), iC2, g13);
+                    const R2 o24 = pfma(psub(pr(A2, A4), g24), iC2, g24);
+                    go[1] = o13.x;
+                    go[3] = o13.y;
+                    go[2] = o24.x;
+                    go[4] = o24.y;
                 }
                 if (inD) {
                     TG* gw = gdst + (size_t)r * pitch + gx;
@@ -730,16 +741,21 @@ struct Sweep {
             }
         }
         if (doA && (STEADY || colvalid)) {
-            rhod_a = ((fa[0] + fa[1]) + (fa[2] + fa[3])) + ((fa[4] + fa[5]) + (fa[6] + fa[7])) + fa[8];
+            // pair sums and differences of (f1, f2) & (f3, f4) and (f5, f6) & (f7, f8)
+            const R2 sA = padd(pr(fa[1], fa[2]), pr(fa[3], fa[4]));   // (f1 + f3, f2 + f4)
+            const R2 dA = psub(pr(fa[1], fa[2]), pr(fa[3], fa[4]));   // (f1 - f3, f2 - f4)
+            const R2 sB = padd(pr(fa[5], fa[6]), pr(fa[7], fa[8]));   // (f5 + f7, f6 + f8)
+            const R2 dB = psub(pr(fa[5], fa[6]), pr(fa[7], fa[8]));   // (f5 - f7, f6 - f8)
+            rhod_a = (fa[0] + (sA.x + sA.y)) + (sB.x + sB.y);
             rho_a = rhod_a + rho_ref;
             ir_a = f_rcp(rho_a);
             const R Td = ((ga[0] + ga[1]) + (ga[2] + ga[3])) + ga[4];
             const R T_a = Td + T_ref;
-            jx_a = (fa[1] - fa[3]) + (fa[5] - fa[6]) + (fa[8] - fa[7]);
-            jy_a = (fa[2] - fa[4]) + (fa[5] + fa[6]) - (fa[7] + fa[8]);
+            jx_a = dA.x + (dB.x - dB.y);    // (f1 - f3) + (f5 - f7) - (f6 - f8)
+            jy_a = dA.y + (dB.x + dB.y);    // (f2 - f4) + (f5 - f7) + (f6 - f8)
             if constexpr (UNIT) {
-                m7_a = (fa[1] + fa[3]) - (fa[2] + fa[4]);
-                m8_a = (fa[5] + fa[7]) - (fa[6] + fa[8]);
+                m7_a = sA.x - sA.y;
+                m8_a = sB.x - sB.y;
             }
             R q2, TdpdT;
             eos_node(P, rho_a, T_a, &q2, &TdpdT);
@@ -815,17 +831,21 @@ struct Sweep {
                     pNE = ghost_psi(P, WR.rho[a2][xr1], WR.rho[a1][cRR], WR.rho[a1][cRL], cot,
                                     WR.T[a1][xr1], &errbits);
                 }
-                // Eq. 9 with varpi(1) = 1/3, varpi(2) = 1/12
-                const R sx = (pE - pW) * R(1.0 / 3.0) + ((pNE - pSW) + (pSE - pNW)) * R(1.0 / 12.0);
-                const R sy = (pN - pS) * R(1.0 / 3.0) + ((pNE - pSW) + (pNW - pSE)) * R(1.0 / 12.0);
-                const R Fmx = P.negG * psip * sx;
-                const R Fmy = P.negG * psip * sy;
-                const R Fx = Fmx;
-                const R Fy = Fmy - P.gravity * (rhop - rho_ave);
+                // Eq. 9 with varpi(1) = 1/3, varpi(2) = 1/12, both components
+                // at once: s = (pE - pW, pN - pS) / 3 + (dA + dB, dA - dB) / 12
+                const R dA = pNE - pSW, dB = pSE - pNW;
+                const R2 sxy = pfma(psub(pr(pE, pN), pr(pW, pS)), pr(R(1.0 / 3.0), R(1.0 / 3.0)),
+                                    pmul(pr(dA + dB, dA - dB), pr(R(1.0 / 12.0), R(1.0 / 12.0))));
+                const R sx = sxy.x, sy = sxy.y;
+                const R gp = P.negG * psip;
+                const R2 Fm = pmul(pr(gp, gp), sxy);
+                const R Fx = Fm.x;
+                const R Fy = Fm.y - P.gravity * (rhop - rho_ave);
                 R ux = R(0), uy = R(0);
                 if (!P.frozen_flow) {
-                    ux = (jxp + R(0.5) * Fx) * irp;
-                    uy = (jyp + R(0.5) * Fy) * irp;
+                    const R2 uu2 = pmul(pfma(pr(Fx, Fy), pr(R(0.5), R(0.5)), pr(jxp, jyp)), pr(irp, irp));
+                    ux = uu2.x;
+                    uy = uu2.y;
                 }
                 R2 uv;
                 uv.x = ux;
@@ -845,37 +865,52 @@ struct Sweep {
                         // collision at m^eq + F/2, so f* = M^{-1} m* needs of f
                         // only rho, j and the stresses m_7, m_8 (Eqs. 5, 7, 8)
                         const R rr = rhop;
-                        const R rux = rr * ux, ruy = rr * uy;
-                        const R ruu = rux * ux + ruy * uy;
-                        const R uF = ux * Fx + uy * Fy;
-                        const R Fm2 = P.negG * P.negG * (sx * sx + sy * sy);
+                        const R2 u2 = pr(ux, uy), F2 = pr(Fx, Fy);
+                        const R2 ru = pmul(pr(rr, rr), u2);          // rho u
+                        const R2 uu = pmul(ru, u2);                  // rho (ux^2, uy^2)
+                        const R2 uFc = pmul(u2, F2);                 // (ux Fx, uy Fy)
+                        const R2 s2 = pmul(sxy, sxy);
+                        const R ruu = uu.x + uu.y;
+                        const R uF = uFc.x + uFc.y;
+                        const R Fm2 = P.negG * P.negG * (s2.x + s2.y);
                         const R m7 = m7p;
                         const R m8 = m8p;
-                        const R F7 = R(2) * (ux * Fx - uy * Fy);
+                        const R F7 = R(2) * (uFc.x - uFc.y);
                         const R F8 = ux * Fy + uy * Fx;
                         // deviation-form m*_e, m*_eps (storage shifts them by
                         // -2 rho_ref and rho_ref)
-                        const R m1s = R(-2) * rhodp + R(3) * (ruu + uF) + R(0.5) * P.sig_e * Fm2;
-                        const R m2s = rhodp - R(3) * (ruu + uF) - R(0.5) * P.sig_eps * Fm2;
+                        const R t3 = R(3) * (ruu + uF);
+                        const R m1s = R(-2) * rhodp + t3 + R(0.5) * P.sig_e * Fm2;
+                        const R m2s = rhodp - t3 - R(0.5) * P.sig_eps * Fm2;
                         const R b0 = rhodp * R(1.0 / 9.0);
-                        const R b1 = m1s * R(1.0 / 36.0), b2 = m2s * R(1.0 / 36.0);
-                        const R b7 = (m7 - P.s_p * (m7 - (rux * ux - ruy * uy)) + P.hs_p * F7) * R(0.25);
-                        const R b8 = (m8 - P.s_p * (m8 - rux * uy) + P.hs_p * F8) * R(0.25);
+                        const R2 b12 = pmul(pr(m1s, m2s), pr(R(1.0 / 36.0), R(1.0 / 36.0)));
+                        const R b1 = b12.x, b2 = b12.y;
+                        const R b7 = (m7 - P.s_p * (m7 - (uu.x - uu.y)) + P.hs_p * F7) * R(0.25);
+                        const R b8 = (m8 - P.s_p * (m8 - ru.x * uy) + P.hs_p * F8) * R(0.25);
                         // j* = j + F; q* = -(j + F) / 1 -> combined axis / diagonal terms
-                        const R jxs = jxp + Fx, jys = jyp + Fy;
-                        const R X3 = jxs * R(1.0 / 3.0), Y3 = jys * R(1.0 / 3.0);
-                        const R X12 = jxs * R(1.0 / 12.0), Y12 = jys * R(1.0 / 12.0);
+                        const R2 js = padd(pr(jxp, jyp), F2);
+                        const R2 XY3 = pmul(js, pr(R(1.0 / 3.0), R(1.0 / 3.0)));
+                        const R2 XY12 = pmul(js, pr(R(1.0 / 12.0), R(1.0 / 12.0)));
                         const R cax = b0 - b1 - R(2) * b2;
                         const R cdg = b0 + R(2) * b1 + b2;
+                        // axis directions: (1, 2) = (cax + b7, cax - b7) + (X3, Y3),
+                        // (3, 4) = the same minus (X3, Y3); diagonals: (5, 8) =
+                        // (cdg + b8, cdg - b8) + (X12 + Y12, X12 - Y12), (7, 6) the
+                        // same minus
+                        const R2 cb = pr(cax + b7, cax - b7);
+                        const R2 f12 = padd(cb, XY3), f34 = psub(cb, XY3);
+                        const R2 db = pr(cdg + b8, cdg - b8);
+                        const R2 sd = pr(XY12.x + XY12.y, XY12.x - XY12.y);
+                        const R2 f58 = padd(db, sd), f76 = psub(db, sd);
                         fsw[0 * NT] = b0 + R(4) * (b2 - b1);
-                        fsw[1 * NT] = cax + X3 + b7;
-                        fsw[2 * NT] = cax + Y3 - b7;
-                        fsw[3 * NT] = cax - X3 + b7;
-                        fsw[4 * NT] = cax - Y3 - b7;
-                        fsw[5 * NT] = cdg + X12 + Y12 + b8;
-                        fsw[6 * NT] = cdg - X12 + Y12 - b8;
-                        fsw[7 * NT] = cdg - X12 - Y12 + b8;
-                        fsw[8 * NT] = cdg + X12 - Y12 - b8;
+                        fsw[1 * NT] = f12.x;
+                        fsw[2 * NT] = f12.y;
+                        fsw[3 * NT] = f34.x;
+                        fsw[4 * NT] = f34.y;
+                        fsw[5 * NT] = f58.x;
+                        fsw[6 * NT] = f76.y;
+                        fsw[7 * NT] = f76.x;
+                        fsw[8 * NT] = f58.y;
                     } else {
                         const R* f = fp;
                         const R rr = rhop;
@@ -959,10 +994,15 @@ struct Sweep {
                     const R A0 = o1.z;
                     const R iC = f_rcp(o1.y * P.cv);
                     go[0] = o0.x + (A0 - o0.x) * iC;
-                    go[1] = o0.y + (A1 - o0.y) * iC;
-                    go[2] = o0.z + (A2 - o0.z) * iC;
-                    go[3] = o0.w + (A3 - o0.w) * iC;
-                    go[4] = o1.x + (A4 - o1.x) * iC;
+                    // as in the staged form: (1, 3) and (2, 4) in pairs
+                    const R2 iC2 = pr(iC, iC);
+                    const R2 g13 = pr(o0.y, o0.w), g24 = pr(o0.z, o1.x);
+                    const R2 o13 = pfma(psub(pr(A1, A3), g13), iC2, g13);
+                    const R2 o24 = pfma(psub(pr(A2, A4), g24), iC2, g24);
+                    go[1] = o13.x;
+                    go[3] = o13.y;
+                    go[2] = o24.x;
+                    go[4] = o24.y;
                 }
                 if (inD) {
                     TG* gw = gdst + (size_t)r * pitch + gx;
