@@ -47,8 +47,8 @@ typedef struct lbm3d_ctx lbm3d_ctx;
 
 /* Device bytes of the state of an nx x ny x nz domain at prec (LBM_FP64 or
  * LBM_FP32): two copies of f (19), g (7) and P, the post-collision g (7) and
- * 14 per-node scalars (rho, T, psi, T dp/dT, j, u, F, |F_m|^2/psi^2).
- * 0 for invalid arguments. */
+ * 14 per-node scalars (rho, T, psi, T dp/dT, j, u, F, |F_m|^2/psi^2), plus
+ * the psi of the two wall ghost layers.  0 for invalid arguments. */
 size_t lbm3d_state_bytes(int nx, int ny, int nz, int prec);
 
 /* Creates a context; stream as in lbm_create (NULL: a library stream).
@@ -82,6 +82,22 @@ int lbm3d_get_populations(lbm3d_ctx* ctx, double* f, double* g, double* P);
  * are those of the sphere (hemisphere when sessile) of that volume.
  * Synchronises. */
 int lbm3d_diagnostics(lbm3d_ctx* ctx, double rho_l, double rho_g, int sessile, lbm_diag* out);
+
+/* Selects how a step runs; the state and its result are the same either way
+ * (same arithmetic per node; sums over nodes in another order).  fused != 0:
+ * one kernel per step marching through the z planes of 16 x 16 node tiles,
+ * zseg planes per CTA (0: chosen from the domain and the device),
+ * recomputing the tile halos, so that f, g and P are read and written once
+ * per step (the least device-memory traffic; bound by latency).  fused == 0
+ * (the default, the faster on a GB300): kernels over the nodes (force and
+ * velocity; collisions with the push of f; the next state's fields), which
+ * keep per-node fields in device memory between them.
+ * The steps of Section 3.2 (Eqs. 5, 9, 11, 20, 24, 39, 49-50) in three
+ * dimensions; the paper has no counterpart of the choice.  Takes effect at
+ * the next lbm3d_step.  LBM_EINVAL for a NULL context or zseg < 0. */
+int lbm3d_set_path(lbm3d_ctx* ctx, int fused, int zseg);
+/* The current path and planes per CTA (either pointer may be NULL). */
+int lbm3d_get_path(const lbm3d_ctx* ctx, int* fused, int* zseg);
 
 long long lbm3d_step_count(const lbm3d_ctx* ctx);
 int lbm3d_sync(lbm3d_ctx* ctx);

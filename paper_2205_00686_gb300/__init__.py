@@ -47,7 +47,8 @@ ABI_FUNCTIONS = (
     "lbm_mass_ring",
     # include/lbm3d.h
     "lbm3d_state_bytes", "lbm3d_create", "lbm3d_init_fields", "lbm3d_step", "lbm3d_get_fields",
-    "lbm3d_get_populations", "lbm3d_diagnostics", "lbm3d_step_count", "lbm3d_sync",
+    "lbm3d_get_populations", "lbm3d_diagnostics", "lbm3d_set_path", "lbm3d_get_path",
+    "lbm3d_step_count", "lbm3d_sync",
     "lbm3d_destroy", "lbm3d_last_error",
 )
 
@@ -174,6 +175,9 @@ def lib():
             "lbm3d_get_populations": ([_vp] * 4, ctypes.c_int),
             "lbm3d_diagnostics": ([_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, D],
                                   ctypes.c_int),
+            "lbm3d_set_path": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "lbm3d_get_path": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                               ctypes.c_int),
             "lbm3d_step_count": ([_vp], ctypes.c_longlong),
             "lbm3d_sync": ([_vp], ctypes.c_int),
             "lbm3d_destroy": ([_vp], None),
@@ -476,6 +480,17 @@ class Domain3:
         _check3(lib().lbm3d_diagnostics(self._h, rho_l, rho_g, int(sessile), ctypes.byref(d)),
                 self._h)
         return {k: getattr(d, k) for k, _ in lbm_diag._fields_}
+
+    def set_path(self, fused: bool = True, zseg: int = 0):
+        """fused: one kernel per step over z-marching tiles (zseg planes per
+        CTA, 0 = automatic); else three kernels per step."""
+        _check3(lib().lbm3d_set_path(self._h, int(bool(fused)), int(zseg)), self._h)
+
+    @property
+    def path(self):
+        f, z = ctypes.c_int(0), ctypes.c_int(0)
+        _check3(lib().lbm3d_get_path(self._h, ctypes.byref(f), ctypes.byref(z)), self._h)
+        return bool(f.value), int(z.value)
 
     @property
     def step_count(self) -> int:

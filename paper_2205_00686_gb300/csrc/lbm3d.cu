@@ -25,6 +25,8 @@
 
 #include <new>
 #include <string>
+#include <type_traits>
+#include <utility>
 
 #include "lbm.h"
 #include "lbm3d.h"
@@ -79,6 +81,90 @@ __host__ __device__ constexpr int mnorm(int k) {
     for (int i = 0; i < 19; ++i) s += mrow(k, i) * mrow(k, i);
     return s;
 }
+// Parity of a moment row under c -> -c: the even rows take the same entry
+// for a direction and its opposite, the odd rows opposite entries (and none
+// for the rest direction).  Pairs are p = 1..9: directions 2p - 1 and 2p.
+__host__ __device__ constexpr bool row_even(int k) {
+    for (int p = 1; p <= 9; ++p)
+        if (mrow(k, 2 * p - 1) != mrow(k, 2 * p)) return false;
+    return true;
+}
+__host__ __device__ constexpr bool row_odd(int k) {
+    if (mrow(k, 0) != 0) return false;
+    for (int p = 1; p <= 9; ++p)
+        if (mrow(k, 2 * p - 1) != -mrow(k, 2 * p)) return false;
+    return true;
+}
+constexpr bool rows_split() {
+    for (int k = 0; k < 19; ++k)
+        if (row_even(k) == row_odd(k)) return false;
+    for (int p = 1; p <= 9; ++p)
+        if (qopp(2 * p - 1) != 2 * p) return false;
+    return true;
+}
+static_assert(rows_split(), "every moment row is even or odd under c -> -c");
+
+// f(integral_constant<int, 0>) ... f(integral_constant<int, N - 1>): the
+// index is a constant in every call, whatever the unroller decides
+template <class F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// m = M f from the pair sums S_p = f_{2p-1} + f_{2p} (even rows) and
+// differences D_p = f_{2p-1} - f_{2p} (odd rows): about half the operations
+// of the plain product
+template <class R>
+__device__ __forceinline__ void moments19(const R (&f)[19], R (&m)[19]) {
+    R S[10], Dp[10];
+    static_for<9>([&](auto pc) {
+        constexpr int p = decltype(pc)::value + 1;
+        S[p] = f[2 * p - 1] + f[2 * p];
+        Dp[p] = f[2 * p - 1] - f[2 * p];
+    });
+    static_for<19>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        R s = 0;
+        if constexpr (mrow(k, 0) != 0) s = R(mrow(k, 0)) * f[0];
+        static_for<9>([&](auto pc) {
+            constexpr int p = decltype(pc)::value + 1;
+            constexpr int c = mrow(k, 2 * p - 1);
+            if constexpr (c != 0) s += R(c) * (row_odd(k) ? Dp[p] : S[p]);
+        });
+        m[k] = s;
+    });
+}
+
+// f += M^T dm: for each pair the even rows give one term E_p for both
+// directions, the odd rows a term O_p of opposite signs
+template <class R>
+__device__ __forceinline__ void add_inverse19(const R (&dm)[19], R (&f)[19]) {
+    R E0 = 0;
+    static_for<19>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if constexpr (mrow(k, 0) != 0) E0 += R(mrow(k, 0)) * dm[k];
+    });
+    f[0] += E0;
+    static_for<9>([&](auto pc) {
+        constexpr int p = decltype(pc)::value + 1;
+        R E = 0, O = 0;
+        static_for<19>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int c = mrow(k, 2 * p - 1);
+            if constexpr (c != 0) {
+                if constexpr (row_odd(k)) O += R(c) * dm[k];
+                else E += R(c) * dm[k];
+            }
+        });
+        f[2 * p - 1] += E + O;
+        f[2 * p] += E - O;
+    });
+}
+
 // D3Q7: rest, +-x, +-y, +-z
 __host__ __device__ constexpr int hx(int i) { return i == 1 ? 1 : (i == 2 ? -1 : 0); }
 __host__ __device__ constexpr int hy(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }
@@ -94,6 +180,7 @@ struct Dom3 {
     void* gstar;
     void* aux;
     void* aux2;
+    void* ghost;      // wall ghost-layer psi [2][ny][pitch] (fused step)
     Ctl* ctl;
     int nx, ny, nz, pitch;
     size_t plane;
@@ -158,6 +245,8 @@ PhysD phys_of(const lbm_params& p) {
 }
 
 __device__ __forceinline__ int wrapn(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// any distance from the domain (tiles wider than a small domain wrap several times)
+__device__ __forceinline__ int wrapm(int i, int n) { const int r = i % n; return r < 0 ? r + n : r; }
 
 template <class R>
 __device__ __forceinline__ size_t nid(const Dom3& D, int x, int y, int z) {
@@ -330,14 +419,7 @@ __global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) 
         for (int i = 0; i < 19; ++i) fn[i * D.plane + n] = f[i];
     } else {
         R m[19];
-#pragma unroll 19
-        for (int kk = 0; kk < 19; ++kk) {
-            R s = 0;
-#pragma unroll 19
-            for (int i = 0; i < 19; ++i)
-                if (mrow(kk, i)) s += R(mrow(kk, i)) * f[i];
-            m[kk] = s;
-        }
+        moments19(f, m);
         // deviation storage: m(abs) = m(dev) + rho_ref M w, M w = (1, -11, 3, 0 ...)
         const R rr = (R)D.rho_ref;
         m[0] += rr;
@@ -375,12 +457,10 @@ __global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) 
             dm[kk] = (-sk[kk] * (m[kk] - meq[kk]) + (R(1) - R(0.5) * sk[kk]) * Fb[kk]) *
                      R(1.0 / mnorm(kk));
         // f* = f + M^T dm, pushed to x + c_i (bounce-back through walls)
+        add_inverse19(dm, f);
 #pragma unroll 19
         for (int i = 0; i < 19; ++i) {
-            R v = f[i];
-#pragma unroll 19
-            for (int kk = 0; kk < 19; ++kk)
-                if (mrow(kk, i)) v += R(mrow(kk, i)) * dm[kk];
+            const R v = f[i];
             if (nbr_solid(nb, qz(i)))
                 fn[qopp(i) * D.plane + n] = v;
             else
@@ -545,6 +625,465 @@ __global__ void k3_advance(Ctl* ctl, double qscale) {
     ctl->step = s + 1;
 }
 
+// ---------------------------------------------------------------------------
+// Fused step: one kernel for the whole step.  A CTA takes an xy tile of
+// TX x TY nodes and a segment [z0, z1) of planes and marches k through the
+// planes; the stages are skewed so that each reads only planes its
+// predecessors have finished (three barriers per plane):
+//   A(k)     rho, j, T, psi, T dp/dT on the tile + 3 halo nodes from f(t), g(t)
+//            (the plane beyond a wall: the ghost-layer psi of Section 3.3)
+//   D5(k-4)  g(t+1) = g + (g*(x - c) - g)/(rho c_v) on the tile      (Eq. 39)
+//   B(k-1)   F_m, F, u on the tile + 2 (Eqs. 9, 11); D3Q19 collision on the
+//            tile + 1 (Eq. 5), each f*_i stored at its destination x + c_i
+//            when that lies in the tile, or bounced back at a wall
+//   C(k-2)   div u, grad T, Q, P^n, S and the D3Q7 collision on the tile + 1
+//            (Eqs. 20, 24, 49-50), g*_i stored at x + c_i (anti-bounce-back
+//            at walls)
+//   D9(k-2)  f(t+1) of the tile from the stored f*, and its density sum
+// Shared-memory rings carry psi, rho, j, T dp/dT and u between the stages,
+// and the post-collision populations live only in shared memory.  Every
+// tile recomputes its halos, so the step reads f, g, P once and writes them
+// once (halo reads are served by L2): no u, F or g* planes, no second read
+// of f for the next state's fields.
+// f*_i is kept for 3 destination planes when c_z = +1 (written two planes
+// ahead of its reader), else 2; g*_5 (+z) likewise.  The bases are closed
+// forms (the +z directions are 5, 11, 14, 15, 18) so that they fold to
+// constants after unrolling; the static_asserts tie them to the slot counts.
+__host__ __device__ constexpr int fslots(int i) { return qz(i) > 0 ? 3 : 2; }
+__host__ __device__ constexpr int fbase(int i) {
+    return 2 * i + (i > 5) + (i > 11) + (i > 14) + (i > 15) + (i > 18);
+}
+__host__ __device__ constexpr int gslots(int i) { return i == 5 ? 3 : 2; }
+__host__ __device__ constexpr int gbase(int i) { return 2 * i + (i > 5); }
+constexpr bool bases_ok() {
+    for (int i = 0; i < 19; ++i)
+        if (fbase(i + 1) - fbase(i) != fslots(i)) return false;
+    for (int i = 0; i < 7; ++i)
+        if (gbase(i + 1) - gbase(i) != gslots(i)) return false;
+    return fbase(0) == 0 && gbase(0) == 0;
+}
+static_assert(bases_ok(), "slot bases");
+// ring slot of plane k (k >= -8)
+__device__ __forceinline__ int ring(int k, int s) { return (k + 24) % s; }
+
+#ifndef K3_TILE_X
+#define K3_TILE_X 16
+#define K3_TILE_Y 16
+#define K3_THREADS 256
+#endif
+template <class R>
+struct Tile3 {
+    static constexpr int TX = K3_TILE_X, TY = K3_TILE_Y, NT = K3_THREADS;
+    static constexpr int W3 = TX + 6, N3 = W3 * (TY + 6);   // tile + 3: psi, rho, j, T dp/dT
+    static constexpr int W2 = TX + 4, N2 = W2 * (TY + 4);   // tile + 2: u
+    static constexpr int W1 = TX + 2, N1 = W1 * (TY + 2);   // tile + 1: collisions
+    static constexpr int NI = TX * TY;                       // the tile
+    static constexpr int NB = N2 - N1;                       // tile + 2 outside tile + 1
+    static constexpr int ELEMS = 15 * N3 + 9 * N2 + (fbase(19) + gbase(7) + 2) * NI;
+    static constexpr size_t BYTES = (size_t)ELEMS * sizeof(R);
+    static constexpr int MIN_BLOCKS = (sizeof(R) == 4 && NT <= 256) ? 2 : 1;
+    static_assert(NI <= NT, "the final stages take one tile node per thread");
+    static_assert(N3 <= 2 * NT && N2 <= 2 * NT && N1 <= 2 * NT, "two passes per stage");
+};
+
+template <class R>
+__global__ void __launch_bounds__(Tile3<R>::NT, Tile3<R>::MIN_BLOCKS)
+k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
+    using G = Tile3<R>;
+    constexpr int TX = G::TX, TY = G::TY, NT = G::NT, W3 = G::W3, N3 = G::N3, W2 = G::W2,
+                  N2 = G::N2, W1 = G::W1, N1 = G::N1, NI = G::NI, NB = G::NB;
+    extern __shared__ __align__(16) unsigned char k3_smem[];
+    R* const s_psi = reinterpret_cast<R*>(k3_smem);   // [3][N3]
+    R* const s_rho = s_psi + 3 * N3;                   // [3][N3]
+    R* const s_j = s_rho + 3 * N3;                     // [2][3][N3]
+    R* const s_tdp = s_j + 6 * N3;                     // [3][N3]
+    R* const s_u = s_tdp + 3 * N3;                     // [3][3][N2]
+    R* const s_f = s_u + 9 * N2;                       // f* by destination plane
+    R* const s_g = s_f + fbase(19) * NI;               // g* by destination plane
+    R* const s_ic = s_g + gbase(7) * NI;               // [2][NI] 1 / (rho c_v)
+
+    const int tid = threadIdx.x;
+    const int ntx = (D.nx + TX - 1) / TX;
+    const int x0 = (int)(blockIdx.x % ntx) * TX, y0 = (int)(blockIdx.x / ntx) * TY;
+    const int z0 = (int)blockIdx.y * zseg, z1 = min(D.nz, z0 + zseg);
+    const long long step = __ldcg(&D.ctl->step);
+    const int par = (int)(step & 1);
+    const R* __restrict__ fc = (const R*)D.f[par];
+    R* __restrict__ fnx = (R*)D.f[par ^ 1];
+    const R* __restrict__ gc = (const R*)D.g[par];
+    R* __restrict__ gnx = (R*)D.g[par ^ 1];
+    const R* __restrict__ Pc = (const R*)D.P[par];
+    R* __restrict__ Pnx = (R*)D.P[par ^ 1];
+    const size_t PL = D.plane, ZS = (size_t)D.ny * D.pitch;
+    const R rho_ref = (R)D.rho_ref, T_ref = (R)D.T_ref;
+    const R rho_ave = L.gravity != R(0) ? (R)(__ldcg(&D.ctl->mass[(step + 2) % 3]) * D.inv_n) : R(0);
+
+    // in-plane offsets of the nodes this thread takes in each stage (the
+    // tile's local coordinates wrap periodically onto the domain)
+    int oA[2], oB[2], bx[2], by[2], oC[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int a = tid + r * NT;
+        const int ax = a < N3 ? a % W3 - 3 : 0, ay = a < N3 ? a / W3 - 3 : 0;
+        oA[r] = wrapm(y0 + ay, D.ny) * D.pitch + wrapm(x0 + ax, D.nx);
+        int lx = 0, ly = 0;
+        if (a < NB) {   // the ring of tile + 2 around tile + 1
+            if (a < W2) { lx = a - 2; ly = -2; }
+            else if (a < 2 * W2) { lx = a - W2 - 2; ly = TY + 1; }
+            else if (a < 2 * W2 + TY + 2) { lx = -2; ly = a - 2 * W2 - 1; }
+            else { lx = TX + 1; ly = a - 2 * W2 - (TY + 2) - 1; }
+        } else if (a < N2) {
+            lx = (a - NB) % W1 - 1;
+            ly = (a - NB) / W1 - 1;
+        }
+        bx[r] = lx;
+        by[r] = ly;
+        oB[r] = wrapm(y0 + ly, D.ny) * D.pitch + wrapm(x0 + lx, D.nx);
+        const int cx = a < N1 ? a % W1 - 1 : 0, cy = a < N1 ? a / W1 - 1 : 0;
+        oC[r] = wrapm(y0 + cy, D.ny) * D.pitch + wrapm(x0 + cx, D.nx);
+    }
+    const int dlx = tid % TX, dly = tid / TX;
+    const int oD = wrapm(y0 + dly, D.ny) * D.pitch + wrapm(x0 + dlx, D.nx);
+    const bool own_xy = tid < NI && x0 + dlx < D.nx && y0 + dly < D.ny;
+    int err = 0;
+    double msum = 0.0;
+
+    for (int k = z0 - 3; k <= z1 + 3; ++k) {
+        // ================= phase 1: A(k), D5(k - 4)
+        if (k <= z1 + 2) {
+            R* const psA = s_psi + ring(k, 3) * N3;
+            if (D.walls && (k < 0 || k >= D.nz)) {
+                if (k == -1 || k == D.nz) {
+                    const R* gp = (const R*)D.ghost + (k < 0 ? (size_t)0 : ZS);
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+                        if (tid + r * NT < N3) psA[tid + r * NT] = gp[oA[r]];
+                }
+            } else {
+                const size_t zo = (size_t)wrapm(k, D.nz) * ZS;
+                R* const rA = s_rho + ring(k, 3) * N3;
+                R* const jA = s_j + ring(k, 2) * 3 * N3;
+                R* const tA = s_tdp + ring(k, 3) * N3;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int a = tid + r * NT;
+                    if (a < N3) {
+                        const size_t n = zo + oA[r];
+                        R f[19], g[7];
+#pragma unroll
+                        for (int i = 0; i < 19; ++i) f[i] = __ldg(fc + i * PL + n);
+#pragma unroll
+                        for (int i = 0; i < 7; ++i) g[i] = __ldg(gc + i * PL + n);
+                        R rd = 0, jx = 0, jy = 0, jz = 0, Td = 0;
+#pragma unroll
+                        for (int i = 0; i < 19; ++i) {
+                            rd += f[i];
+                            if (qx(i)) jx += R(qx(i)) * f[i];
+                            if (qy(i)) jy += R(qy(i)) * f[i];
+                            if (qz(i)) jz += R(qz(i)) * f[i];
+                        }
+#pragma unroll
+                        for (int i = 0; i < 7; ++i) Td += g[i];
+                        const R rho = rd + rho_ref, T = Td + T_ref;
+                        R q2, tdp;
+                        eos_node(P, rho, T, &q2, &tdp);
+                        if (!(q2 >= R(0))) err |= (q2 != q2) ? ERR_NONFINITE : ERR_PSI;
+                        if (!(T == T) || !(rho == rho)) err |= ERR_NONFINITE;
+                        psA[a] = f_sqrt(q2);
+                        rA[a] = rho;
+                        jA[a] = jx;
+                        jA[N3 + a] = jy;
+                        jA[2 * N3 + a] = jz;
+                        tA[a] = tdp;
+                    }
+                }
+            }
+        }
+        {
+            const int q = k - 4;
+            if (q >= z0 && q < z1 && own_xy) {
+                const size_t n = (size_t)q * ZS + oD;
+                const R iC = s_ic[ring(q, 2) * NI + tid];
+#pragma unroll
+                for (int i = 0; i < 7; ++i) {
+                    const R go = gc[i * PL + n];
+                    gnx[i * PL + n] = L.frozen_thermal
+                                          ? go
+                                          : go + (s_g[(gbase(i) + ring(q, gslots(i))) * NI + tid] - go) * iC;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ================= phase 2: B(k - 1)
+        {
+            const int p = k - 1;
+            if (p >= z0 - 2 && p <= z1 + 1 && !(D.walls && (p < 0 || p >= D.nz))) {
+                // f* is needed from planes z0 - 1 .. z1 only
+                const bool coll = !L.frozen_flow && p >= z0 - 1 && p <= z1;
+                const size_t zo = (size_t)wrapm(p, D.nz) * ZS;
+                const R* const psm = s_psi + ring(p - 1, 3) * N3;
+                const R* const ps0 = s_psi + ring(p, 3) * N3;
+                const R* const psp = s_psi + ring(p + 1, 3) * N3;
+                const R* const rB = s_rho + ring(p, 3) * N3;
+                const R* const jB = s_j + ring(p, 2) * 3 * N3;
+                R* const uB = s_u + ring(p, 3) * 3 * N2;
+#pragma unroll 1
+                for (int r = 0; r < 2; ++r) {
+                    const int b = tid + r * NT;
+                    if (b >= N2) break;
+                    // (selects, not indexing: the arrays stay in registers)
+                    const int lx = r ? bx[1] : bx[0], ly = r ? by[1] : by[0];
+                    const int c3 = (ly + 3) * W3 + lx + 3;
+                    R sx = 0, sy = 0, sz = 0;
+#pragma unroll
+                    for (int i = 1; i < 19; ++i) {
+                        const R* pp = qz(i) < 0 ? psm : (qz(i) > 0 ? psp : ps0);
+                        const R pn = pp[c3 + qy(i) * W3 + qx(i)];
+                        const R wv = qc2(i) == 1 ? R(1.0 / 6.0) : R(1.0 / 12.0);
+                        if (qx(i)) sx += wv * pn * R(qx(i));
+                        if (qy(i)) sy += wv * pn * R(qy(i));
+                        if (qz(i)) sz += wv * pn * R(qz(i));
+                    }
+                    const R psi = ps0[c3], rho = rB[c3];
+                    const R Fx = P.negG * psi * sx, Fy = P.negG * psi * sy;
+                    const R Fz = P.negG * psi * sz - L.gravity * (rho - rho_ave);
+                    R ux = 0, uy = 0, uz = 0;
+                    if (!L.frozen_flow) {
+                        const R ir = R(1) / rho;
+                        ux = (jB[c3] + R(0.5) * Fx) * ir;
+                        uy = (jB[N3 + c3] + R(0.5) * Fy) * ir;
+                        uz = (jB[2 * N3 + c3] + R(0.5) * Fz) * ir;
+                    }
+                    const int c2 = (ly + 2) * W2 + lx + 2;
+                    uB[c2] = ux;
+                    uB[N2 + c2] = uy;
+                    uB[2 * N2 + c2] = uz;
+                    if (!coll || b < NB) continue;
+                    // ---- D3Q19 MRT collision in moment space
+                    const R Fm2 = P.negG * P.negG * (sx * sx + sy * sy + sz * sz);
+                    const size_t n = zo + (r ? oB[1] : oB[0]);
+                    R f[19];
+#pragma unroll
+                    for (int i = 0; i < 19; ++i) f[i] = fc[i * PL + n];
+                    R m[19];
+                    moments19(f, m);
+                    m[0] += rho_ref;
+                    m[1] += R(-11) * rho_ref;
+                    m[2] += R(3) * rho_ref;
+                    const R uu = ux * ux + uy * uy + uz * uz;
+                    const R uF = ux * Fx + uy * Fy + uz * Fz;
+                    R meq[19], Fb[19], sk[19];
+                    meq[0] = rho;                            Fb[0] = 0;                  sk[0] = 0;
+                    meq[1] = rho * (R(-11) + R(19) * uu);    Fb[1] = R(38) * uF + L.sig_e3 * Fm2;  sk[1] = L.s_e;
+                    meq[2] = rho * (R(3) - R(5.5) * uu);     Fb[2] = R(-11) * uF;        sk[2] = L.s_eps;
+                    meq[3] = rho * ux;                       Fb[3] = Fx;                 sk[3] = 1;
+                    meq[4] = R(-2.0 / 3.0) * rho * ux;       Fb[4] = R(-2.0 / 3.0) * Fx; sk[4] = L.s_q;
+                    meq[5] = rho * uy;                       Fb[5] = Fy;                 sk[5] = 1;
+                    meq[6] = R(-2.0 / 3.0) * rho * uy;       Fb[6] = R(-2.0 / 3.0) * Fy; sk[6] = L.s_q;
+                    meq[7] = rho * uz;                       Fb[7] = Fz;                 sk[7] = 1;
+                    meq[8] = R(-2.0 / 3.0) * rho * uz;       Fb[8] = R(-2.0 / 3.0) * Fz; sk[8] = L.s_q;
+                    const R pxx = R(3) * ux * ux - uu, axx = R(2) * ux * Fx - uy * Fy - uz * Fz;
+                    const R pww = uy * uy - uz * uz, aww = uy * Fy - uz * Fz;
+                    meq[9] = rho * pxx;                      Fb[9] = R(2) * axx;         sk[9] = L.s_p;
+                    meq[10] = R(-0.5) * rho * pxx;           Fb[10] = -axx;              sk[10] = L.s_q;
+                    meq[11] = rho * pww;                     Fb[11] = R(2) * aww;        sk[11] = L.s_p;
+                    meq[12] = R(-0.5) * rho * pww;           Fb[12] = -aww;              sk[12] = L.s_q;
+                    meq[13] = rho * ux * uy;                 Fb[13] = ux * Fy + uy * Fx; sk[13] = L.s_p;
+                    meq[14] = rho * uy * uz;                 Fb[14] = uy * Fz + uz * Fy; sk[14] = L.s_p;
+                    meq[15] = rho * ux * uz;                 Fb[15] = ux * Fz + uz * Fx; sk[15] = L.s_p;
+                    meq[16] = 0;                             Fb[16] = 0;                 sk[16] = L.s_q;
+                    meq[17] = 0;                             Fb[17] = 0;                 sk[17] = L.s_q;
+                    meq[18] = 0;                             Fb[18] = 0;                 sk[18] = L.s_q;
+                    R dm[19];
+#pragma unroll
+                    for (int kk = 0; kk < 19; ++kk)
+                        dm[kk] = (-sk[kk] * (m[kk] - meq[kk]) + (R(1) - R(0.5) * sk[kk]) * Fb[kk]) *
+                                 R(1.0 / mnorm(kk));
+                    add_inverse19(dm, f);   // f* = f + M^T dm
+                    const bool in_tile = lx >= 0 && lx < TX && ly >= 0 && ly < TY;
+                    static_for<19>([&](auto ic) {
+                        constexpr int i = decltype(ic)::value;
+                        const R v = f[i];
+                        const int dz = p + qz(i);
+                        if (D.walls && (dz < 0 || dz >= D.nz)) {
+                            // halfway bounce-back: f_opp(i)(x, t+1) = f*_i(x)
+                            if (in_tile)
+                                s_f[(fbase(qopp(i)) + ring(p, fslots(qopp(i)))) * NI + ly * TX + lx] = v;
+                        } else {
+                            const int dx = lx + qx(i), dy = ly + qy(i);
+                            if (dx >= 0 && dx < TX && dy >= 0 && dy < TY)
+                                s_f[(fbase(i) + ring(dz, fslots(i))) * NI + dy * TX + dx] = v;
+                        }
+                    });
+                }
+            }
+        }
+        __syncthreads();
+
+        // ================= phase 3: C(k - 2), D9(k - 2)
+        {
+            const int q = k - 2;
+            if (q >= z0 - 1 && q <= z1 && !(D.walls && (q < 0 || q >= D.nz))) {
+                const size_t zo = (size_t)wrapm(q, D.nz) * ZS;
+                const bool own_z = q >= z0 && q < z1;
+                const bool lo_wall = D.walls && q == 0, hi_wall = D.walls && q == D.nz - 1;
+                const R* const um = s_u + ring(q - 1, 3) * 3 * N2;
+                const R* const u0 = s_u + ring(q, 3) * 3 * N2;
+                const R* const up = s_u + ring(q + 1, 3) * 3 * N2;
+                const R* const rC = s_rho + ring(q, 3) * N3;
+                const R* const tC = s_tdp + ring(q, 3) * N3;
+#pragma unroll 1
+                for (int r = 0; r < 2; ++r) {
+                    const int c = tid + r * NT;
+                    if (c >= N1) break;
+                    const int lx = c % W1 - 1, ly = c / W1 - 1;
+                    const int c2 = (ly + 2) * W2 + lx + 2, c3 = (ly + 3) * W3 + lx + 3;
+                    // div u: (1/c_s^2) sum_i w_i c_i . u(x + c_i); walls carry u = 0
+                    R divu = 0;
+#pragma unroll
+                    for (int i = 1; i < 19; ++i) {
+                        if ((qz(i) < 0 && lo_wall) || (qz(i) > 0 && hi_wall)) continue;
+                        const R* us = (qz(i) < 0 ? um : (qz(i) > 0 ? up : u0)) + c2 + qy(i) * W2 + qx(i);
+                        R cu = 0;
+                        if (qx(i)) cu += R(qx(i)) * us[0];
+                        if (qy(i)) cu += R(qy(i)) * us[N2];
+                        if (qz(i)) cu += R(qz(i)) * us[2 * N2];
+                        divu += R(3.0 * qw(i)) * cu;
+                    }
+                    const size_t n = zo + (r ? oC[1] : oC[0]);
+                    R g[7];
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) g[i] = gc[i * PL + n];
+                    const R ux = u0[c2], uy = u0[N2 + c2], uz = u0[2 * N2 + c2];
+                    const R rho = rC[c3], TdpdT = tC[c3];
+                    // grad T from the local first moments: c^_s^2 d_a T = -vs1 m^_a
+                    const R m1 = g[1] - g[2], m2 = g[3] - g[4], m3 = g[5] - g[6];
+                    const R kT = -L.vs1 / L.cs2h;
+                    const R dTx = kT * m1, dTy = kT * m2, dTz = kT * m3;
+                    const R C = rho * L.cv;
+                    const R Q = -(C * (ux * dTx + uy * dTy + uz * dTz) + TdpdT * divu);
+                    const R Pn = Q / C;
+                    const R Qs = step == 0 ? Q : Q + R(0.5) * (Q - C * Pc[n]);
+                    const bool in_tile = lx >= 0 && lx < TX && ly >= 0 && ly < TY;
+                    const int ti = ly * TX + lx;
+                    if (in_tile) {
+                        if (own_z && x0 + lx < D.nx && y0 + ly < D.ny) Pnx[n] = Pn;
+                        s_ic[ring(q, 2) * NI + ti] = R(1) / (rho * L.cv);
+                    }
+                    // ---- D3Q7 MRT collision (deviation form), closed-form inverse
+                    const R Td = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+                    const R m4 = g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+                    const R m5 = (g[1] + g[2]) - (g[3] + g[4]);
+                    const R m6 = (g[3] + g[4]) - (g[5] + g[6]);
+                    const R wd = L.w7_1 * R(6);
+                    const R s0 = Td - L.vs0 * (Td - Td) + Qs;
+                    const R s1 = m1 - L.vs1 * m1, s2 = m2 - L.vs1 * m2, s3 = m3 - L.vs1 * m3;
+                    const R s4 = m4 - L.vs3 * (m4 - wd * Td) + wd * Qs;
+                    const R s5 = m5 - L.vs4 * m5, s6 = m6 - L.vs4 * m6;
+                    const R bq = (s4 - s5 + s6) * R(1.0 / 3.0);
+                    const R aq = bq + s5, cq = bq - s6;
+                    R gs[7];
+                    gs[0] = s0 - s4;
+                    gs[1] = R(0.5) * (aq + s1);
+                    gs[2] = R(0.5) * (aq - s1);
+                    gs[3] = R(0.5) * (bq + s2);
+                    gs[4] = R(0.5) * (bq - s2);
+                    gs[5] = R(0.5) * (cq + s3);
+                    gs[6] = R(0.5) * (cq - s3);
+                    // in-plane directions land in this plane
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        const int dx = lx + hx(i), dy = ly + hy(i);
+                        if (dx >= 0 && dx < TX && dy >= 0 && dy < TY)
+                            s_g[(gbase(i) + ring(q, 2)) * NI + dy * TX + dx] = gs[i];
+                    }
+                    if (in_tile) {
+                        // +z lands on the plane above; at the top wall it returns
+                        // as -z: A = 2 w^ T_w - g*_5 (Dirichlet) or g*_5 (adiabatic)
+                        if (hi_wall)
+                            s_g[(gbase(6) + ring(q, 2)) * NI + ti] =
+                                D.therm[1] == T_DIRICHLET
+                                    ? R(2) * L.w7_1 * (R)(D.T_edge[1] - D.T_ref) - gs[5]
+                                    : gs[5];
+                        else
+                            s_g[(gbase(5) + ring(q + 1, 3)) * NI + ti] = gs[5];
+                        if (lo_wall)
+                            s_g[(gbase(5) + ring(q, 3)) * NI + ti] =
+                                D.therm[0] == T_DIRICHLET
+                                    ? R(2) * L.w7_1 * (R)(D.T_edge[0] - D.T_ref) - gs[6]
+                                    : gs[6];
+                        else
+                            s_g[(gbase(6) + ring(q - 1, 2)) * NI + ti] = gs[6];
+                    }
+                }
+            }
+        }
+        {
+            const int q = k - 2;
+            if (q >= z0 && q < z1 && own_xy) {
+                const size_t n = (size_t)q * ZS + oD;
+                R rd = 0;
+#pragma unroll
+                for (int i = 0; i < 19; ++i) {
+                    const R v = L.frozen_flow ? fc[i * PL + n]
+                                              : s_f[(fbase(i) + ring(q, fslots(i))) * NI + tid];
+                    fnx[i * PL + n] = v;
+                    rd += v;
+                }
+                if (use_mass) msum += (double)(rd + rho_ref);
+            }
+        }
+        __syncthreads();
+    }
+
+    // density sum of the new state for the buoyancy of the next step
+    if (use_mass) {
+        double* red = reinterpret_cast<double*>(k3_smem);
+        for (int o = 16; o > 0; o >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, o);
+        if ((tid & 31) == 0) red[tid >> 5] = msum;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += red[w];
+            massq_add(&D.ctl->massq[(step + 1) % 3], s, massq_scale(D.inv_n));
+        }
+    }
+    if (err) atomicOr(&D.ctl->err, err);
+}
+
+// psi of the ghost layers beyond the two walls (Section 3.3) from the current
+// state: rho_ghost = rho(layer 2) + tan(pi/2 - theta) |tangential difference of
+// rho at layer 1|, at the temperature of layer 1
+template <class R>
+__global__ void k3_ghost(Dom3 D, Phys<R> P) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int e = blockIdx.z;
+    if (x >= D.nx || y >= D.ny) return;
+    const int par = (int)(__ldcg(&D.ctl->step) & 1);
+    const R* fc = (const R*)D.f[par];
+    const R* gc = (const R*)D.g[par];
+    const int z1 = e == 0 ? 0 : D.nz - 1, z2 = e == 0 ? 1 : D.nz - 2;
+    auto rho_at = [&](int xx, int yy, int zz) {
+        const size_t n = nid<R>(D, xx, yy, zz);
+        R rd = 0;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) rd += fc[i * D.plane + n];
+        return rd + (R)D.rho_ref;
+    };
+    const R dx = rho_at(wrapn(x + 1, D.nx), y, z1) - rho_at(wrapn(x - 1, D.nx), y, z1);
+    const R dy = rho_at(x, wrapn(y + 1, D.ny), z1) - rho_at(x, wrapn(y - 1, D.ny), z1);
+    const R rg = rho_at(x, y, z2) + (R)D.cot * rsq(dx * dx + dy * dy);
+    const size_t n1 = nid<R>(D, x, y, z1);
+    R Td = 0;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Td += gc[i * D.plane + n1];
+    const R q2 = psi2_of(P, rg, Td + (R)D.T_ref);
+    if (!(q2 >= R(0))) atomicOr(&D.ctl->err, (q2 != q2) ? ERR_NONFINITE : ERR_PSI);
+    ((R*)D.ghost)[((size_t)e * D.ny + y) * D.pitch + x] = f_sqrt(q2);
+}
+
 // populations f = f^eq(rho, u), g = w^ T as deviations; P = 0
 template <class R>
 __global__ void k3_init(Dom3 D, Lat3<R> L, const double* rho, const double* ux,
@@ -616,6 +1155,9 @@ struct lbm3d_ctx {
     Ctl* ctl = nullptr;
     Dom3 D;
     cudaGraphExec_t graph = nullptr;
+    bool fused = false;      // one fused kernel per step (else three kernels)
+    int zseg = 0;            // planes per CTA of the fused step
+    bool aux_stale = false;  // the per-node planes lag the state (fused steps)
     long long step = 0;
     bool initialized = false;
     int sticky = LBM_OK;
@@ -633,8 +1175,25 @@ size_t pitch_for(int nx) { return ((size_t)nx + 31) / 32 * 32; }
 size_t bytes_for(int nx, int ny, int nz, int prec) {
     const size_t es = prec == LBM_FP64 ? 8 : 4;
     const size_t plane = pitch_for(nx) * ny * nz;
-    // f 2 x 19, g 2 x 7, g* 7, P 2, aux 7, aux2 7
-    return plane * es * (38 + 14 + 7 + 2 + A_N + B_N);
+    // f 2 x 19, g 2 x 7, g* 7, P 2, aux 7, aux2 7, two ghost-layer planes
+    return plane * es * (38 + 14 + 7 + 2 + A_N + B_N) + 2 * pitch_for(nx) * ny * es;
+}
+
+// planes per CTA of the fused step: enough (tile, segment) units for about
+// four per resident CTA, segments of at least 16 planes
+int auto_zseg(int nx, int ny, int nz, int prec) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 148;
+    const int tx = Tile3<float>::TX, ty = Tile3<float>::TY;
+    const long long tiles = (long long)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+    const long long slots = (long long)sms * (prec == LBM_FP64 ? Tile3<double>::MIN_BLOCKS
+                                                              : Tile3<float>::MIN_BLOCKS);
+    const long long nseg = (4 * slots + tiles - 1) / tiles;
+    int zs = (int)((nz + nseg - 1) / nseg);
+    if (zs < 16) zs = 16;
+    return zs > nz ? nz : zs;
 }
 
 int set_err3(lbm3d_ctx* c, int code, const char* msg) {
@@ -653,7 +1212,28 @@ dim3 blk3() { return dim3(32, 4, 1); }
 dim3 grd3(const lbm3d_ctx* c) { return dim3((c->nx + 31) / 32, (c->ny + 3) / 4, c->nz); }
 
 template <class R>
+int launch_fused(lbm3d_ctx* c) {
+    using G = Tile3<R>;
+    Phys<R> P = make_phys<R>(phys_of(c->params));
+    Lat3<R> L = make_lat3<R>(c->params);
+    if (c->D.walls)
+        k3_ghost<R><<<dim3((c->nx + 31) / 32, (c->ny + 3) / 4, 2), blk3(), 0, c->stream>>>(c->D, P);
+    const dim3 grid((unsigned)(((c->nx + G::TX - 1) / G::TX) * ((c->ny + G::TY - 1) / G::TY)),
+                    (unsigned)((c->nz + c->zseg - 1) / c->zseg));
+    k3_fused<R><<<grid, G::NT, G::BYTES, c->stream>>>(c->D, P, L, c->zseg, c->params.gravity != 0.0);
+    k3_advance<<<1, 1, 0, c->stream>>>(c->ctl, massq_scale(c->D.inv_n));
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// the per-node planes (rho, T, psi, T dp/dT, j) of the current state
+template <class R>
+void launch_macro(lbm3d_ctx* c) {
+    k3_macro<R><<<grd3(c), blk3(), 0, c->stream>>>(c->D, make_phys<R>(phys_of(c->params)), 0, 0);
+}
+
+template <class R>
 int launch_step(lbm3d_ctx* c) {
+    if (c->fused) return launch_fused<R>(c);
     Phys<R> P = make_phys<R>(phys_of(c->params));
     Lat3<R> L = make_lat3<R>(c->params);
     const dim3 b = blk3(), g = grd3(c);
@@ -696,10 +1276,12 @@ int export_fields(lbm3d_ctx* c) {
     if (rc) return rc;
     const dim3 b = blk3(), g = grd3(c);
     if (c->prec == LBM_FP64) {
+        launch_macro<double>(c);
         k3_force<double><<<g, b, 0, c->stream>>>(c->D, make_phys<double>(phys_of(c->params)),
                                                    make_lat3<double>(c->params));
         k3_export<double><<<g, b, 0, c->stream>>>(c->D, make_lat3<double>(c->params), 0, c->host_buf);
     } else {
+        launch_macro<float>(c);
         k3_force<float><<<g, b, 0, c->stream>>>(c->D, make_phys<float>(phys_of(c->params)),
                                                   make_lat3<float>(c->params));
         k3_export<float><<<g, b, 0, c->stream>>>(c->D, make_lat3<float>(c->params), 0, c->host_buf);
@@ -768,7 +1350,8 @@ int lbm3d_create(int nx, int ny, int nz, const lbm_params* params, const lbm3d_b
     D.gstar = m + off; off += 7 * plane * es;
     for (int p = 0; p < 2; ++p) { D.P[p] = m + off; off += plane * es; }
     D.aux = m + off; off += A_N * plane * es;
-    D.aux2 = m + off;
+    D.aux2 = m + off; off += B_N * plane * es;
+    D.ghost = m + off;
     D.ctl = c->ctl;
     D.nx = nx;
     D.ny = ny;
@@ -784,8 +1367,15 @@ int lbm3d_create(int nx, int ny, int nz, const lbm_params* params, const lbm3d_b
     D.rho_ref = 1.0;
     D.T_ref = 0.0;
     D.inv_n = 1.0 / ((double)nx * ny * nz);
+    c->zseg = auto_zseg(nx, ny, nz, prec);
+    if (prec == LBM_FP64)
+        e = cudaFuncSetAttribute(k3_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Tile3<double>::BYTES);
+    else
+        e = cudaFuncSetAttribute(k3_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Tile3<float>::BYTES);
     // the pitch padding is never read, but keep it defined
-    e = cudaMemset(c->mem, 0, total);
+    if (e == cudaSuccess) e = cudaMemset(c->mem, 0, total);
     if (e != cudaSuccess) {
         lbm3d_destroy(c);
         return LBM_ECUDA;
@@ -848,6 +1438,7 @@ int lbm3d_init_fields(lbm3d_ctx* c, const double* rho, const double* ux, const d
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;   // the launch arguments carry rho_ref / T_ref
     c->step = 0;
+    c->aux_stale = false;
     c->sticky = LBM_OK;
     c->initialized = true;
     c->err.clear();
@@ -858,6 +1449,12 @@ int lbm3d_step(lbm3d_ctx* c, int n) {
     if (!c || n < 0) return LBM_EINVAL;
     if (!c->initialized) return set_err3(c, LBM_ESTATE, "lbm3d_step before lbm3d_init_fields");
     if (c->sticky) return c->sticky;
+    if (n == 0) return LBM_OK;
+    if (!c->fused && c->aux_stale) {   // the three-kernel step starts from these planes
+        if (c->prec == LBM_FP64) launch_macro<double>(c);
+        else launch_macro<float>(c);
+    }
+    c->aux_stale = c->fused;
     const int kLen = 32;
     int left = n;
     if (left >= kLen) {
@@ -953,6 +1550,26 @@ int lbm3d_diagnostics(lbm3d_ctx* c, double rho_l, double rho_g, int sessile, lbm
 }
 
 long long lbm3d_step_count(const lbm3d_ctx* c) { return c ? c->step : -1; }
+
+int lbm3d_set_path(lbm3d_ctx* c, int fused, int zseg) {
+    if (!c || zseg < 0) return LBM_EINVAL;
+    const bool f = fused != 0;
+    const int zs = zseg == 0 ? auto_zseg(c->nx, c->ny, c->nz, c->prec) : (zseg > c->nz ? c->nz : zseg);
+    if (f != c->fused || zs != c->zseg) {
+        if (c->graph) cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    c->fused = f;
+    c->zseg = zs;
+    return LBM_OK;
+}
+
+int lbm3d_get_path(const lbm3d_ctx* c, int* fused, int* zseg) {
+    if (!c) return LBM_EINVAL;
+    if (fused) *fused = c->fused ? 1 : 0;
+    if (zseg) *zseg = c->zseg;
+    return LBM_OK;
+}
 
 int lbm3d_sync(lbm3d_ctx* c) {
     if (!c) return LBM_EINVAL;

@@ -27,12 +27,13 @@ def with_T_bump(c, amp=0.02, seed=21):
     return c
 
 
-def run_both(c, steps, prec, chunks=None):
+def run_both(c, steps, prec, chunks=None, fused=True, zseg=0):
     import paper_2205_00686_gb300 as lbm
     o = O.Sim3(c.nx, c.ny, c.nz, c.params, c.bc)
     o.init(*c.fields())
     o.step(steps)
     d = lbm.Domain3(c.nx, c.ny, c.nz, c.params, c.bc, prec=prec)
+    d.set_path(fused, zseg)
     d.init_fields(*c.fields())
     for k in (chunks or [steps]):
         d.step(k)
@@ -59,10 +60,11 @@ def cases():
     return out
 
 
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "three_kernels"])
 @pytest.mark.parametrize("name", ["periodic", "walls_dirichlet_gravity", "sessile_adiabatic_top"])
-def test_fp64_matches_oracle(name):
+def test_fp64_matches_oracle(name, fused):
     c = cases()[name]
-    d, o = run_both(c, 200, "fp64")
+    d, o = run_both(c, 200, "fp64", fused=fused, zseg=7 if fused else 0)
     fe = fields_err(d, o)
     assert max(fe.values()) <= 1e-10, (name, fe)
     gf, gg, gP = d.populations()
@@ -72,10 +74,11 @@ def test_fp64_matches_oracle(name):
     d.close()
 
 
-def test_fp32_matches_oracle_after_1000_steps():
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "three_kernels"])
+def test_fp32_matches_oracle_after_1000_steps(fused):
     c = with_T_bump(W.droplet3d(14, 14, 20, R=4.5, amp=1e-3, p=W.params(gravity=1e-5)))
     c.bc = W.wall_bc3(0.9 * W.TC, 0.86 * W.TC, theta_deg=80.0)
-    d, o = run_both(c, 1000, "fp32")
+    d, o = run_both(c, 1000, "fp32", fused=fused)
     fe = fields_err(d, o)
     assert max(fe.values()) <= 2e-4, fe
     d.close()
@@ -161,15 +164,80 @@ def test_invariants_at_256_cubed():
         d.close()
 
 
+@pytest.mark.parametrize("zseg", [0, 16])
 @pytest.mark.parametrize("walls", [False, True])
-def test_multi_block_domain_matches_oracle(walls):
-    """A domain of several 32 x 4 thread blocks with ragged x and y edges
-    (45 x 9) and 70 planes, periodic z and between walls, against the oracle
-    in FP64 after 30 steps."""
+def test_multi_block_domain_matches_oracle(walls, zseg):
+    """A domain of several tiles with ragged x and y edges (45 x 9: three 16 x
+    16 tiles, the last 13 wide, all cut at y = 9) and 70 planes, periodic z
+    and between walls, against the oracle in FP64 after 30 steps; zseg 16
+    cuts z into segments of 16 planes and a ragged one of 6."""
     Tc = W.TC
     c = with_T_bump(W.droplet3d(45, 9, 70, R=6.0, amp=1e-3, p=W.params(gravity=2e-5)))
     if walls:
         c.bc = W.wall_bc3(0.95 * Tc, 0.88 * Tc, theta_deg=70.0)
-    d, o = run_both(c, 30, "fp64")
+    d, o = run_both(c, 30, "fp64", zseg=zseg)
     e = fields_err(d, o)
     assert max(e.values()) <= 1e-10, e
+    gf, gg, gP = d.populations()
+    of, og, oP = o.populations()
+    assert P.rel_err(gf, of) <= 1e-12 and P.rel_err(gg, og) <= 1e-12
+    d.close()
+
+
+@pytest.mark.parametrize("walls", [False, True])
+@pytest.mark.parametrize("zseg", [1, 2, 3])
+def test_domain_smaller_than_a_tile(walls, zseg):
+    """5 x 3 x 7 nodes inside one 16 x 16 tile (the tile's halos wrap several
+    times around x and y) with segments of 1, 2 and 3 planes, against the
+    oracle in FP64 after 25 steps."""
+    Tc = W.TC
+    c = with_T_bump(W.droplet3d(5, 3, 7, R=1.5, amp=1e-3, p=W.params(gravity=2e-5)))
+    if walls:
+        c.bc = W.wall_bc3(0.93 * Tc, 0.9 * Tc, theta_deg=75.0, adiabatic=(True, False))
+    d, o = run_both(c, 25, "fp64", zseg=zseg)
+    e = fields_err(d, o)
+    assert max(e.values()) <= 1e-10, e
+    gf, gg, gP = d.populations()
+    of, og, oP = o.populations()
+    assert P.rel_err(gf, of) <= 1e-12 and P.rel_err(gg, og) <= 1e-12
+    d.close()
+
+
+def test_switching_paths_mid_run_matches_oracle():
+    """Fused, three-kernel and fused steps again (12 + 9 + 14) continue one
+    another: the per-node planes and the density ring are handed over."""
+    import paper_2205_00686_gb300 as lbm
+    c = cases()["walls_dirichlet_gravity"]
+    o = O.Sim3(c.nx, c.ny, c.nz, c.params, c.bc)
+    o.init(*c.fields())
+    o.step(35)
+    d = lbm.Domain3(c.nx, c.ny, c.nz, c.params, c.bc, prec="fp64")
+    d.init_fields(*c.fields())
+    for fused, n in ((True, 12), (False, 9), (True, 14)):
+        d.set_path(fused, 5)
+        assert d.path == (fused, 5)
+        d.step(n)
+    e = fields_err(d, o)
+    assert max(e.values()) <= 1e-10, e
+    d.close()
+
+
+def test_fused_fp32_equals_itself_for_any_segment_length():
+    """In FP32 the segment length changes only which CTA computes a node,
+    never its arithmetic: without buoyancy (whose density sum is rounded per
+    CTA) the populations are bitwise equal for zseg 5, 16 and the whole
+    column, walls and wetting included."""
+    import paper_2205_00686_gb300 as lbm
+    c = cases()["sessile_adiabatic_top"]
+    assert float(c.params.get("gravity", 0.0)) == 0.0
+    out = []
+    for zs in (5, 16, c.nz):
+        d = lbm.Domain3(c.nx, c.ny, c.nz, c.params, c.bc, prec="fp32")
+        d.set_path(True, zs)
+        d.init_fields(*c.fields())
+        d.step(40)
+        out.append(d.populations())
+        d.close()
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
