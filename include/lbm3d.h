@@ -46,9 +46,9 @@ typedef struct {
 typedef struct lbm3d_ctx lbm3d_ctx;
 
 /* Device bytes of the state of an nx x ny x nz domain at prec (LBM_FP64 or
- * LBM_FP32): two copies of f (19), g (7) and P, the post-collision g (7) and
- * 14 per-node scalars (rho, T, psi, T dp/dT, j, u, F, |F_m|^2/psi^2), plus
- * the psi of the two wall ghost layers.  0 for invalid arguments. */
+ * LBM_FP32): two copies of f (19), g (7) and P, 15 per-node scalars (rho, T,
+ * psi, T dp/dT, j, 1/(rho c_v), u, F, |F_m|^2/psi^2), plus the psi of the two
+ * wall ghost layers.  0 for invalid arguments. */
 size_t lbm3d_state_bytes(int nx, int ny, int nz, int prec);
 
 /* Creates a context; stream as in lbm_create (NULL: a library stream).

@@ -3,20 +3,21 @@
 // energy moment) + D3Q7 temperature lattice with the rho c_v-weighted
 // streaming of Eq. 39, x and y periodic, z periodic or walls.
 //
-// One step is three kernels over the nodes (plus a one-thread counter
-// update), because every stage needs neighbours of the previous one and a
-// fused sweep with recomputed halos does not fit shared memory in 3-D:
+// The default step is three kernels over the nodes (plus a one-thread
+// counter update), because every stage needs neighbours of the previous one:
 //   k3_force    psi of the 18 neighbours (ghost layer at walls) -> F_m, F,
-//               u = (j + F/2)/rho, |F_m|^2/psi^2               (Eqs. 9, 11)
+//               u = (j + F/2)/rho, |F_m|^2/psi^2                (Eqs. 9, 11)
 //   k3_collide  div u (neighbour u), grad T (local moments), Q, P^n, S;
 //               D3Q19 and D3Q7 collisions; f* pushed to its destination
-//               (bounce-back at walls); g* and P^n stored    (Eqs. 5, 20, 24, 39)
-//   k3_blend    g(t+1) = g + (g*(y - c) - g)/(rho c_v) pulled (anti-bounce-back
-//               at walls); then rho, j, T, psi, T dp/dT of the new state
-//               from f(t+1) and g(t+1), and the density sum for buoyancy
-// Per node and step (FP32) this moves about twice the 216 B of one read and
-// one write of the state: f is read again after the push to build the next
-// state's rho, j and psi, and u, F pass through memory once.
+//               (bounce-back at walls); g*_i blended into the destination's
+//               g(t+1) = g + (g* - g)/(rho c_v) (anti-bounce-back at walls),
+//               P^n stored                          (Eqs. 5, 20, 24, 39)
+//   k3_macro    rho, j, T, psi, T dp/dT, 1/(rho c_v) of the new state from
+//               f(t+1), g(t+1), and the density sum for buoyancy
+// Per node and step (FP32) this moves about 1.9 times the 216 B of one read
+// and one write of the state: f is read again after the push to build the
+// next state's fields, and u, F and the per-node fields pass through memory.
+// k3_fused (below) does the whole step in one kernel with recomputed halos.
 //
 // Populations are stored as deviations f_i - w_i rho_ref and g_i - w^_i T_ref.
 // Planes are [q][nz][ny][pitch], 64-bit offsets.
@@ -170,14 +171,13 @@ __host__ __device__ constexpr int hx(int i) { return i == 1 ? 1 : (i == 2 ? -1 :
 __host__ __device__ constexpr int hy(int i) { return i == 3 ? 1 : (i == 4 ? -1 : 0); }
 __host__ __device__ constexpr int hz(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
 
-enum { A_RHO = 0, A_T, A_PSI, A_TDPDT, A_JX, A_JY, A_JZ, A_N };   // aux planes
-enum { B_UX = 0, B_UY, B_UZ, B_FX, B_FY, B_FZ, B_FM2, B_N };      // aux2 planes
+enum { A_RHO = 0, A_T, A_PSI, A_TDPDT, A_JX, A_JY, A_JZ, A_IC, A_N };   // aux: 1/(rho c_v) last
+enum { B_UX = 0, B_UY, B_UZ, B_FX, B_FY, B_FZ, B_FM2, B_N };            // aux2 planes
 
 struct Dom3 {
     void* f[2];
     void* g[2];
     void* P[2];
-    void* gstar;
     void* aux;
     void* aux2;
     void* ghost;      // wall ghost-layer psi [2][ny][pitch] (fused step)
@@ -314,6 +314,35 @@ __device__ R psi_nb(const Dom3& D, const Phys<R>& P, int x, int y, int z, int* e
     return f_sqrt(q2);
 }
 
+// F_m from the psi of the 18 neighbours and F = F_m + F_b at node n
+// (Eqs. 9, 11); |F_m|^2 / psi^2 for the sigma term
+template <class R>
+__device__ __forceinline__ void force_at(const Dom3& D, const Phys<R>& P, const Lat3<R>& L,
+                                         int x, int y, int z, size_t n, const Nbr& nb,
+                                         long long step, int* err, R* F, R* Fm2) {
+    const R* A = (const R*)D.aux;
+    const R* psi_p = A + A_PSI * D.plane;
+    R sx = 0, sy = 0, sz = 0;
+#pragma unroll 19
+    for (int i = 1; i < 19; ++i) {
+        const R wv = qc2(i) == 1 ? R(1.0 / 6.0) : R(1.0 / 12.0);
+        // beyond a wall the neighbour is the ghost layer (Section 3.3)
+        const R pn = nbr_solid(nb, qz(i))
+                         ? psi_nb<R>(D, P, x + qx(i), y + qy(i), z + qz(i), err)
+                         : psi_p[(size_t)((long long)n + nbr_off(nb, qx(i), qy(i), qz(i)))];
+        if (qx(i)) sx += wv * pn * R(qx(i));
+        if (qy(i)) sy += wv * pn * R(qy(i));
+        if (qz(i)) sz += wv * pn * R(qz(i));
+    }
+    const R psi = psi_p[n];
+    const R rho = A[A_RHO * D.plane + n];
+    const R rho_ave = L.gravity != R(0) ? (R)(__ldcg(&D.ctl->mass[(step + 2) % 3]) * D.inv_n) : R(0);
+    F[0] = P.negG * psi * sx;
+    F[1] = P.negG * psi * sy;
+    F[2] = P.negG * psi * sz - L.gravity * (rho - rho_ave);
+    *Fm2 = P.negG * P.negG * (sx * sx + sy * sy + sz * sz);
+}
+
 template <class R>
 __global__ void __launch_bounds__(128) k3_force(Dom3 D, Phys<R> P, Lat3<R> L) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -324,40 +353,23 @@ __global__ void __launch_bounds__(128) k3_force(Dom3 D, Phys<R> P, Lat3<R> L) {
     R* B = (R*)D.aux2;
     const size_t n = nid<R>(D, x, y, z);
     const Nbr nb = nbr_offsets(D, x, y, z);
-    const R* psi_p = A + A_PSI * D.plane;
     int err = 0;
-    R sx = 0, sy = 0, sz = 0;
-#pragma unroll 19
-    for (int i = 1; i < 19; ++i) {
-        const R wv = qc2(i) == 1 ? R(1.0 / 6.0) : R(1.0 / 12.0);
-        // beyond a wall the neighbour is the ghost layer (Section 3.3)
-        const R pn = nbr_solid(nb, qz(i))
-                         ? psi_nb<R>(D, P, x + qx(i), y + qy(i), z + qz(i), &err)
-                         : psi_p[(size_t)((long long)n + nbr_off(nb, qx(i), qy(i), qz(i)))];
-        if (qx(i)) sx += wv * pn * R(qx(i));
-        if (qy(i)) sy += wv * pn * R(qy(i));
-        if (qz(i)) sz += wv * pn * R(qz(i));
-    }
-    const R psi = psi_p[n];
-    const R rho = A[A_RHO * D.plane + n];
-    const long long step = __ldcg(&D.ctl->step);
-    const R rho_ave = L.gravity != R(0) ? (R)(__ldcg(&D.ctl->mass[(step + 2) % 3]) * D.inv_n) : R(0);
-    const R Fx = P.negG * psi * sx, Fy = P.negG * psi * sy;
-    const R Fz = P.negG * psi * sz - L.gravity * (rho - rho_ave);
+    R F[3], Fm2;
+    force_at<R>(D, P, L, x, y, z, n, nb, __ldcg(&D.ctl->step), &err, F, &Fm2);
     R ux = 0, uy = 0, uz = 0;
     if (!L.frozen_flow) {
-        const R ir = R(1) / rho;
-        ux = (A[A_JX * D.plane + n] + R(0.5) * Fx) * ir;
-        uy = (A[A_JY * D.plane + n] + R(0.5) * Fy) * ir;
-        uz = (A[A_JZ * D.plane + n] + R(0.5) * Fz) * ir;
+        const R ir = R(1) / A[A_RHO * D.plane + n];
+        ux = (A[A_JX * D.plane + n] + R(0.5) * F[0]) * ir;
+        uy = (A[A_JY * D.plane + n] + R(0.5) * F[1]) * ir;
+        uz = (A[A_JZ * D.plane + n] + R(0.5) * F[2]) * ir;
     }
     B[B_UX * D.plane + n] = ux;
     B[B_UY * D.plane + n] = uy;
     B[B_UZ * D.plane + n] = uz;
-    B[B_FX * D.plane + n] = Fx;
-    B[B_FY * D.plane + n] = Fy;
-    B[B_FZ * D.plane + n] = Fz;
-    B[B_FM2 * D.plane + n] = P.negG * P.negG * (sx * sx + sy * sy + sz * sz);
+    B[B_FX * D.plane + n] = F[0];
+    B[B_FY * D.plane + n] = F[1];
+    B[B_FZ * D.plane + n] = F[2];
+    B[B_FM2 * D.plane + n] = Fm2;
     if (err) atomicOr(&D.ctl->err, err);
 }
 
@@ -375,19 +387,19 @@ __global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) 
     const R* gc = (const R*)D.g[par];
     const R* Pc = (const R*)D.P[par];
     R* Pn_out = (R*)D.P[par ^ 1];
-    R* gs = (R*)D.gstar;
+    R* gn = (R*)D.g[par ^ 1];
     const R* A = (const R*)D.aux;
     const R* B = (const R*)D.aux2;
     const size_t n = nid<R>(D, x, y, z);
     const R rho = A[A_RHO * D.plane + n];
     const R TdpdT = A[A_TDPDT * D.plane + n];
     const R ux = B[B_UX * D.plane + n], uy = B[B_UY * D.plane + n], uz = B[B_UZ * D.plane + n];
-    const R Fx = B[B_FX * D.plane + n], Fy = B[B_FY * D.plane + n], Fz = B[B_FZ * D.plane + n];
-    const R Fm2 = B[B_FM2 * D.plane + n];
     R g[7];
 #pragma unroll 19
     for (int i = 0; i < 7; ++i) g[i] = gc[i * D.plane + n];
 
+    const R Fx = B[B_FX * D.plane + n], Fy = B[B_FY * D.plane + n], Fz = B[B_FZ * D.plane + n];
+    const R Fm2 = B[B_FM2 * D.plane + n];
     const Nbr nb = nbr_offsets(D, x, y, z);
     // div u: (1/c_s^2) sum_i w_i c_i . u(x + c_i); walls carry u = 0
     R divu = 0;
@@ -482,13 +494,38 @@ __global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) 
         const R s5 = m5 - L.vs4 * m5, s6 = m6 - L.vs4 * m6;
         const R b = (s4 - s5 + s6) * R(1.0 / 3.0);
         const R a = b + s5, c = b - s6;
-        gs[0 * D.plane + n] = s0 - s4;
-        gs[1 * D.plane + n] = R(0.5) * (a + s1);
-        gs[2 * D.plane + n] = R(0.5) * (a - s1);
-        gs[3 * D.plane + n] = R(0.5) * (b + s2);
-        gs[4 * D.plane + n] = R(0.5) * (b - s2);
-        gs[5 * D.plane + n] = R(0.5) * (c + s3);
-        gs[6 * D.plane + n] = R(0.5) * (c - s3);
+        R gs[7];
+        gs[0] = s0 - s4;
+        gs[1] = R(0.5) * (a + s1);
+        gs[2] = R(0.5) * (a - s1);
+        gs[3] = R(0.5) * (b + s2);
+        gs[4] = R(0.5) * (b - s2);
+        gs[5] = R(0.5) * (c + s3);
+        gs[6] = R(0.5) * (c - s3);
+        // weighted streaming (Eq. 39) from this node's side: g*_i lands on
+        // x = y + c_i as g_i(x) + (g*_i - g_i(x)) / (rho(x) c_v), with g_i(x)
+        // and rho(x) those of the current state; through a wall g*_i
+        // returns to this node as the opposite direction, A = 2 w^ T_w - g*_i
+        // (Dirichlet) or g*_i (adiabatic)
+        if (L.frozen_thermal) {
+#pragma unroll 7
+            for (int i = 0; i < 7; ++i) gn[i * D.plane + n] = g[i];
+        } else {
+#pragma unroll 7
+            for (int i = 0; i < 7; ++i) {
+                if ((i == 5 && nb.zhi) || (i == 6 && nb.zlo)) {
+                    const int e = i == 5 ? 1 : 0, o = i == 5 ? 6 : 5;
+                    const R Ai = D.therm[e] == T_DIRICHLET
+                                     ? R(2) * L.w7_1 * (R)(D.T_edge[e] - D.T_ref) - gs[i]
+                                     : gs[i];
+                    gn[o * D.plane + n] = g[o] + (Ai - g[o]) * A[A_IC * D.plane + n];
+                } else {
+                    const size_t m = (size_t)((long long)n + nbr_off(nb, hx(i), hy(i), hz(i)));
+                    const R go = gc[i * D.plane + m];
+                    gn[i * D.plane + m] = go + (gs[i] - go) * A[A_IC * D.plane + m];
+                }
+            }
+        }
     }
     Pn_out[n] = Pn;
 }
@@ -496,7 +533,7 @@ __global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) 
 // ---------------------------------------------------------------------------
 // macroscopic fields of a node from its (deviation) populations
 template <class R>
-__device__ __forceinline__ void macro_node(const Dom3& D, const Phys<R>& P, const R* f19,
+__device__ __forceinline__ void macro_node(const Dom3& D, const Phys<R>& P, R cv, const R* f19,
                                            const R* g7, size_t n, int* err, R* rho_out) {
     R* A = (R*)D.aux;
     R rd = 0, jx = 0, jy = 0, jz = 0, Td = 0;
@@ -518,6 +555,7 @@ __device__ __forceinline__ void macro_node(const Dom3& D, const Phys<R>& P, cons
     A[A_T * D.plane + n] = T;
     A[A_PSI * D.plane + n] = f_sqrt(q2);
     A[A_TDPDT * D.plane + n] = TdpdT;
+    A[A_IC * D.plane + n] = R(1) / (rho * cv);
     A[A_JX * D.plane + n] = jx;
     A[A_JY * D.plane + n] = jy;
     A[A_JZ * D.plane + n] = jz;
@@ -535,8 +573,11 @@ __device__ __forceinline__ void add_mass(const Dom3& D, double v, int slot) {
     if (t == 0) massq_add(&D.ctl->massq[slot], red[0] + red[1] + red[2] + red[3], massq_scale(D.inv_n));
 }
 
+// macroscopic fields of the current state (next = 0) or of the state the
+// step in progress has just written (next = 1), with its density sum into
+// slot (step + next) % 3 for buoyancy
 template <class R>
-__global__ void __launch_bounds__(128) k3_blend(Dom3 D, Phys<R> P, Lat3<R> L, int use_mass) {
+__global__ void __launch_bounds__(128) k3_macro(Dom3 D, Phys<R> P, R cv, int use_mass, int next) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -544,60 +585,7 @@ __global__ void __launch_bounds__(128) k3_blend(Dom3 D, Phys<R> P, Lat3<R> L, in
     double msum = 0.0;
     const long long step = __ldcg(&D.ctl->step);
     if (in) {
-        const int par = (int)(step & 1);
-        const R* gc = (const R*)D.g[par];
-        R* gn = (R*)D.g[par ^ 1];
-        const R* fn = (const R*)D.f[par ^ 1];
-        const R* gs = (const R*)D.gstar;
-        const R* A = (const R*)D.aux;
-        const size_t n = nid<R>(D, x, y, z);
-        const Nbr nb = nbr_offsets(D, x, y, z);
-        const R iC = R(1) / (A[A_RHO * D.plane + n] * L.cv);
-        R g[7];
-#pragma unroll 19
-        for (int i = 0; i < 7; ++i) {
-            const R go = gc[i * D.plane + n];
-            if (L.frozen_thermal) {
-                g[i] = go;
-            } else {
-                R Ai;
-                if (nbr_solid(nb, -hz(i))) {
-                    // i = 5 enters through the bottom, i = 6 through the top;
-                    // the outgoing partner is the opposite direction
-                    const int e = i == 5 ? 0 : 1;
-                    const R gopp = gs[(i == 5 ? 6 : 5) * D.plane + n];
-                    Ai = D.therm[e] == T_DIRICHLET
-                             ? R(2) * L.w7_1 * (R)(D.T_edge[e] - D.T_ref) - gopp
-                             : gopp;
-                } else {
-                    Ai = gs[i * D.plane + (size_t)((long long)n + nbr_off(nb, -hx(i), -hy(i), -hz(i)))];
-                }
-                g[i] = go + (Ai - go) * iC;
-            }
-            gn[i * D.plane + n] = g[i];
-        }
-        R f[19];
-#pragma unroll 19
-        for (int i = 0; i < 19; ++i) f[i] = fn[i * D.plane + n];
-        int err = 0;
-        R rho;
-        macro_node<R>(D, P, f, g, n, &err, &rho);
-        if (err) atomicOr(&D.ctl->err, err);
-        msum = (double)rho;
-    }
-    if (use_mass) add_mass(D, in ? msum : 0.0, (int)((step + 1) % 3));
-}
-
-// macroscopic fields of the state at initialisation
-template <class R>
-__global__ void __launch_bounds__(128) k3_macro(Dom3 D, Phys<R> P, int use_mass, int slot) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    const bool in = x < D.nx && y < D.ny;
-    double msum = 0.0;
-    if (in) {
-        const int par = (int)(__ldcg(&D.ctl->step) & 1);
+        const int par = (int)(step & 1) ^ next;
         const R* fc = (const R*)D.f[par];
         const R* gc = (const R*)D.g[par];
         const size_t n = nid<R>(D, x, y, z);
@@ -608,11 +596,11 @@ __global__ void __launch_bounds__(128) k3_macro(Dom3 D, Phys<R> P, int use_mass,
         for (int i = 0; i < 7; ++i) g[i] = gc[i * D.plane + n];
         int err = 0;
         R rho;
-        macro_node<R>(D, P, f, g, n, &err, &rho);
+        macro_node<R>(D, P, cv, f, g, n, &err, &rho);
         if (err) atomicOr(&D.ctl->err, err);
         msum = (double)rho;
     }
-    if (use_mass) add_mass(D, in ? msum : 0.0, slot);
+    if (use_mass) add_mass(D, in ? msum : 0.0, (int)((step + next) % 3));
 }
 
 // end of a step: publish the density sum the step's blend accumulated (the
@@ -1175,8 +1163,8 @@ size_t pitch_for(int nx) { return ((size_t)nx + 31) / 32 * 32; }
 size_t bytes_for(int nx, int ny, int nz, int prec) {
     const size_t es = prec == LBM_FP64 ? 8 : 4;
     const size_t plane = pitch_for(nx) * ny * nz;
-    // f 2 x 19, g 2 x 7, g* 7, P 2, aux 7, aux2 7, two ghost-layer planes
-    return plane * es * (38 + 14 + 7 + 2 + A_N + B_N) + 2 * pitch_for(nx) * ny * es;
+    // f 2 x 19, g 2 x 7, P 2, aux 8, aux2 7, two ghost-layer planes
+    return plane * es * (38 + 14 + 2 + A_N + B_N) + 2 * pitch_for(nx) * ny * es;
 }
 
 // planes per CTA of the fused step: enough (tile, segment) units for about
@@ -1228,7 +1216,8 @@ int launch_fused(lbm3d_ctx* c) {
 // the per-node planes (rho, T, psi, T dp/dT, j) of the current state
 template <class R>
 void launch_macro(lbm3d_ctx* c) {
-    k3_macro<R><<<grd3(c), blk3(), 0, c->stream>>>(c->D, make_phys<R>(phys_of(c->params)), 0, 0);
+    k3_macro<R><<<grd3(c), blk3(), 0, c->stream>>>(c->D, make_phys<R>(phys_of(c->params)),
+                                                   (R)c->params.cv, 0, 0);
 }
 
 template <class R>
@@ -1239,7 +1228,8 @@ int launch_step(lbm3d_ctx* c) {
     const dim3 b = blk3(), g = grd3(c);
     k3_force<R><<<g, b, 0, c->stream>>>(c->D, P, L);
     k3_collide<R><<<g, b, 0, c->stream>>>(c->D, P, L);
-    k3_blend<R><<<g, b, 0, c->stream>>>(c->D, P, L, c->params.gravity != 0.0);
+    k3_macro<R><<<g, b, 0, c->stream>>>(c->D, make_phys<R>(phys_of(c->params)), (R)c->params.cv,
+                                        c->params.gravity != 0.0, 1);
     k3_advance<<<1, 1, 0, c->stream>>>(c->ctl, massq_scale(c->D.inv_n));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -1347,7 +1337,6 @@ int lbm3d_create(int nx, int ny, int nz, const lbm_params* params, const lbm3d_b
     size_t off = 0;
     for (int p = 0; p < 2; ++p) { D.f[p] = m + off; off += 19 * plane * es; }
     for (int p = 0; p < 2; ++p) { D.g[p] = m + off; off += 7 * plane * es; }
-    D.gstar = m + off; off += 7 * plane * es;
     for (int p = 0; p < 2; ++p) { D.P[p] = m + off; off += plane * es; }
     D.aux = m + off; off += A_N * plane * es;
     D.aux2 = m + off; off += B_N * plane * es;
@@ -1416,12 +1405,14 @@ int lbm3d_init_fields(lbm3d_ctx* c, const double* rho, const double* ux, const d
         k3_init<double><<<g, b, 0, c->stream>>>(c->D, make_lat3<double>(c->params), c->host_buf,
                                                 c->host_buf + N, c->host_buf + 2 * N,
                                                 c->host_buf + 3 * N, c->host_buf + 4 * N);
-        k3_macro<double><<<g, b, 0, c->stream>>>(c->D, make_phys<double>(phys_of(c->params)), um, 0);
+        k3_macro<double><<<g, b, 0, c->stream>>>(c->D, make_phys<double>(phys_of(c->params)),
+                                                 c->params.cv, um, 0);
     } else {
         k3_init<float><<<g, b, 0, c->stream>>>(c->D, make_lat3<float>(c->params), c->host_buf,
                                                c->host_buf + N, c->host_buf + 2 * N,
                                                c->host_buf + 3 * N, c->host_buf + 4 * N);
-        k3_macro<float><<<g, b, 0, c->stream>>>(c->D, make_phys<float>(phys_of(c->params)), um, 0);
+        k3_macro<float><<<g, b, 0, c->stream>>>(c->D, make_phys<float>(phys_of(c->params)),
+                                                (float)c->params.cv, um, 0);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err3(c, e, "init kernels");
     // the initial density sum (accumulated into massq[0]) is read by step 0

@@ -57,10 +57,10 @@ def test_binding_loads_and_reports_sizes(built_lib):
 
 def test_3d_state_bytes(built_lib):
     import paper_2205_00686_gb300 as lbm
-    # 75 planes of [nz][ny][pitch] (pitch = nx rounded up to 32) and the two
+    # 69 planes of [nz][ny][pitch] (pitch = nx rounded up to 32) and the two
     # wall ghost layers [2][ny][pitch]
-    assert lbm.lbm3d_state_bytes(64, 48, 40, "fp32") == (75 * 40 + 2) * 64 * 48 * 4
-    assert lbm.lbm3d_state_bytes(33, 2, 3, "fp64") == (75 * 3 + 2) * 64 * 2 * 8
+    assert lbm.lbm3d_state_bytes(64, 48, 40, "fp32") == (69 * 40 + 2) * 64 * 48 * 4
+    assert lbm.lbm3d_state_bytes(33, 2, 3, "fp64") == (69 * 3 + 2) * 64 * 2 * 8
     assert lbm.lbm3d_state_bytes(8, 8, 8, "fp32_g16") == 0
 
 
