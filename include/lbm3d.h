@@ -84,14 +84,15 @@ int lbm3d_get_populations(lbm3d_ctx* ctx, double* f, double* g, double* P);
 int lbm3d_diagnostics(lbm3d_ctx* ctx, double rho_l, double rho_g, int sessile, lbm_diag* out);
 
 /* Selects how a step runs; the state and its result are the same either way
- * (same arithmetic per node; sums over nodes in another order).  fused != 0:
- * one kernel per step marching through the z planes of 16 x 16 node tiles,
- * zseg planes per CTA (0: chosen from the domain and the device),
- * recomputing the tile halos, so that f, g and P are read and written once
- * per step (the least device-memory traffic; bound by latency).  fused == 0
- * (the default, the faster on a GB300): kernels over the nodes (force and
- * velocity; collisions with the push of f; the next state's fields), which
- * keep per-node fields in device memory between them.
+ * (same arithmetic per node; sums over nodes in another order).  fused != 0
+ * (the default in FP32): one kernel per step marching through the z planes
+ * of 16 x 16 node tiles, zseg planes per CTA (0: chosen from the domain and
+ * the device), recomputing the fields the stencils need around each tile, so
+ * that f, g and P are read and written once per step.  fused == 0 (the
+ * default in FP64, where the recomputation costs more than the traffic it
+ * saves): kernels over the nodes (force and velocity; collisions with the
+ * push of f and g; the next state's fields), which keep per-node fields in
+ * device memory between them.
  * The steps of Section 3.2 (Eqs. 5, 9, 11, 20, 24, 39, 49-50) in three
  * dimensions; the paper has no counterpart of the choice.  Takes effect at
  * the next lbm3d_step.  LBM_EINVAL for a NULL context or zseg < 0. */

@@ -616,41 +616,25 @@ __global__ void k3_advance(Ctl* ctl, double qscale) {
 // ---------------------------------------------------------------------------
 // Fused step: one kernel for the whole step.  A CTA takes an xy tile of
 // TX x TY nodes and a segment [z0, z1) of planes and marches k through the
-// planes; the stages are skewed so that each reads only planes its
-// predecessors have finished (three barriers per plane):
-//   A(k)     rho, j, T, psi, T dp/dT on the tile + 3 halo nodes from f(t), g(t)
-//            (the plane beyond a wall: the ghost-layer psi of Section 3.3)
-//   D5(k-4)  g(t+1) = g + (g*(x - c) - g)/(rho c_v) on the tile      (Eq. 39)
-//   B(k-1)   F_m, F, u on the tile + 2 (Eqs. 9, 11); D3Q19 collision on the
-//            tile + 1 (Eq. 5), each f*_i stored at its destination x + c_i
-//            when that lies in the tile, or bounced back at a wall
-//   C(k-2)   div u, grad T, Q, P^n, S and the D3Q7 collision on the tile + 1
-//            (Eqs. 20, 24, 49-50), g*_i stored at x + c_i (anti-bounce-back
-//            at walls)
-//   D9(k-2)  f(t+1) of the tile from the stored f*, and its density sum
-// Shared-memory rings carry psi, rho, j, T dp/dT and u between the stages,
-// and the post-collision populations live only in shared memory.  Every
-// tile recomputes its halos, so the step reads f, g, P once and writes them
-// once (halo reads are served by L2): no u, F or g* planes, no second read
-// of f for the next state's fields.
-// f*_i is kept for 3 destination planes when c_z = +1 (written two planes
-// ahead of its reader), else 2; g*_5 (+z) likewise.  The bases are closed
-// forms (the +z directions are 5, 11, 14, 15, 18) so that they fold to
-// constants after unrolling; the static_asserts tie them to the slot counts.
-__host__ __device__ constexpr int fslots(int i) { return qz(i) > 0 ? 3 : 2; }
-__host__ __device__ constexpr int fbase(int i) {
-    return 2 * i + (i > 5) + (i > 11) + (i > 14) + (i > 15) + (i > 18);
-}
-__host__ __device__ constexpr int gslots(int i) { return i == 5 ? 3 : 2; }
-__host__ __device__ constexpr int gbase(int i) { return 2 * i + (i > 5); }
-constexpr bool bases_ok() {
-    for (int i = 0; i < 19; ++i)
-        if (fbase(i + 1) - fbase(i) != fslots(i)) return false;
-    for (int i = 0; i < 7; ++i)
-        if (gbase(i + 1) - gbase(i) != gslots(i)) return false;
-    return fbase(0) == 0 && gbase(0) == 0;
-}
-static_assert(bases_ok(), "slot bases");
+// planes, the stages skewed so that each reads only planes its predecessors
+// have finished (two barriers per plane):
+//   A(k)     rho, j, T, psi, T dp/dT, 1/(rho c_v) on the tile + 2 halo nodes
+//            from f(t), g(t) (beyond a wall: the ghost-layer psi, Section 3.3)
+//   C(k-3)   on the tile: div u, grad T, Q, P^n, S and the D3Q7 collision
+//            (Eqs. 20, 24, 49-50); g*_i blended into the destination's
+//            g(t+1) = g + (g* - g)/(rho c_v) (Eq. 39; anti-bounce-back at
+//            walls)
+//   B(k-1)   F_m, F, u on the tile + 1 (Eqs. 9, 11); on the tile the D3Q19
+//            collision (Eq. 5) with f*_i pushed to x + c_i (bounce-back at
+//            walls) and the new state's density sum
+// Shared-memory rings carry psi, rho, 1/(rho c_v), j, T dp/dT and u between
+// the stages.  Each node is collided by the CTA that owns it, which writes
+// its post-collision populations straight to their destinations in f(t+1)
+// and g(t+1); only the fields the stencils need (two halo nodes of psi, one
+// of u) are recomputed around the tile.  The step reads f, g, P once and
+// writes them once (the halo and destination reads come from L2): no u, F
+// or g* planes and no second read of f for the next state's fields.
+
 // ring slot of plane k (k >= -8)
 __device__ __forceinline__ int ring(int k, int s) { return (k + 24) % s; }
 
@@ -662,33 +646,33 @@ __device__ __forceinline__ int ring(int k, int s) { return (k + 24) % s; }
 template <class R>
 struct Tile3 {
     static constexpr int TX = K3_TILE_X, TY = K3_TILE_Y, NT = K3_THREADS;
-    static constexpr int W3 = TX + 6, N3 = W3 * (TY + 6);   // tile + 3: psi, rho, j, T dp/dT
-    static constexpr int W2 = TX + 4, N2 = W2 * (TY + 4);   // tile + 2: u
-    static constexpr int W1 = TX + 2, N1 = W1 * (TY + 2);   // tile + 1: collisions
-    static constexpr int NI = TX * TY;                       // the tile
-    static constexpr int NB = N2 - N1;                       // tile + 2 outside tile + 1
-    static constexpr int ELEMS = 15 * N3 + 9 * N2 + (fbase(19) + gbase(7) + 2) * NI;
+    static constexpr int W2 = TX + 4, N2 = W2 * (TY + 4);   // tile + 2: fields, psi
+    static constexpr int W1 = TX + 2, N1 = W1 * (TY + 2);   // tile + 1: F, u
+    static constexpr int NI = TX * TY;                       // the tile: collisions
+    static constexpr int NB = N1 - NI;                       // tile + 1 outside the tile
+    // psi 3, rho 4, 1/(rho c_v) 5, j 2 x 3, T dp/dT 4 planes of tile + 2; u 3 x 3 of tile + 1
+    static constexpr int ELEMS = 22 * N2 + 9 * N1;
     static constexpr size_t BYTES = (size_t)ELEMS * sizeof(R);
-    static constexpr int MIN_BLOCKS = (sizeof(R) == 4 && NT <= 256) ? 2 : 1;
-    static_assert(NI <= NT, "the final stages take one tile node per thread");
-    static_assert(N3 <= 2 * NT && N2 <= 2 * NT && N1 <= 2 * NT, "two passes per stage");
+    // FP32: three CTAs per SM (80 registers, no spills; 11.7 against 10.1
+    // GLUPS with two at 120 registers; four spill); FP64 needs ~240 registers
+    static constexpr int MIN_BLOCKS = (sizeof(R) == 4 && NT <= 256) ? 3 : 1;
+    static_assert(NI <= NT, "the collisions take one tile node per thread");
+    static_assert(N2 <= 2 * NT && N1 <= 2 * NT, "two passes per stage");
 };
 
 template <class R>
 __global__ void __launch_bounds__(Tile3<R>::NT, Tile3<R>::MIN_BLOCKS)
 k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
     using G = Tile3<R>;
-    constexpr int TX = G::TX, TY = G::TY, NT = G::NT, W3 = G::W3, N3 = G::N3, W2 = G::W2,
-                  N2 = G::N2, W1 = G::W1, N1 = G::N1, NI = G::NI, NB = G::NB;
+    constexpr int TX = G::TX, TY = G::TY, NT = G::NT, W2 = G::W2, N2 = G::N2, W1 = G::W1,
+                  N1 = G::N1, NI = G::NI, NB = G::NB;
     extern __shared__ __align__(16) unsigned char k3_smem[];
-    R* const s_psi = reinterpret_cast<R*>(k3_smem);   // [3][N3]
-    R* const s_rho = s_psi + 3 * N3;                   // [3][N3]
-    R* const s_j = s_rho + 3 * N3;                     // [2][3][N3]
-    R* const s_tdp = s_j + 6 * N3;                     // [3][N3]
-    R* const s_u = s_tdp + 3 * N3;                     // [3][3][N2]
-    R* const s_f = s_u + 9 * N2;                       // f* by destination plane
-    R* const s_g = s_f + fbase(19) * NI;               // g* by destination plane
-    R* const s_ic = s_g + gbase(7) * NI;               // [2][NI] 1 / (rho c_v)
+    R* const s_psi = reinterpret_cast<R*>(k3_smem);   // [3][N2]
+    R* const s_rho = s_psi + 3 * N2;                   // [4][N2]
+    R* const s_ic = s_rho + 4 * N2;                    // [5][N2] 1 / (rho c_v)
+    R* const s_j = s_ic + 5 * N2;                      // [2][3][N2]
+    R* const s_tdp = s_j + 6 * N2;                     // [4][N2]
+    R* const s_u = s_tdp + 4 * N2;                     // [3][3][N1]
 
     const int tid = threadIdx.x;
     const int ntx = (D.nx + TX - 1) / TX;
@@ -706,56 +690,61 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
     const R rho_ref = (R)D.rho_ref, T_ref = (R)D.T_ref;
     const R rho_ave = L.gravity != R(0) ? (R)(__ldcg(&D.ctl->mass[(step + 2) % 3]) * D.inv_n) : R(0);
 
-    // in-plane offsets of the nodes this thread takes in each stage (the
-    // tile's local coordinates wrap periodically onto the domain)
-    int oA[2], oB[2], bx[2], by[2], oC[2];
+    // in-plane offsets of the nodes this thread takes in stage A (the tile's
+    // local coordinates wrap periodically onto the domain)
+    int oA[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int a = tid + r * NT;
-        const int ax = a < N3 ? a % W3 - 3 : 0, ay = a < N3 ? a / W3 - 3 : 0;
+        const int ax = a < N2 ? a % W2 - 2 : 0, ay = a < N2 ? a / W2 - 2 : 0;
         oA[r] = wrapm(y0 + ay, D.ny) * D.pitch + wrapm(x0 + ax, D.nx);
-        int lx = 0, ly = 0;
-        if (a < NB) {   // the ring of tile + 2 around tile + 1
-            if (a < W2) { lx = a - 2; ly = -2; }
-            else if (a < 2 * W2) { lx = a - W2 - 2; ly = TY + 1; }
-            else if (a < 2 * W2 + TY + 2) { lx = -2; ly = a - 2 * W2 - 1; }
-            else { lx = TX + 1; ly = a - 2 * W2 - (TY + 2) - 1; }
-        } else if (a < N2) {
-            lx = (a - NB) % W1 - 1;
-            ly = (a - NB) / W1 - 1;
-        }
-        bx[r] = lx;
-        by[r] = ly;
-        oB[r] = wrapm(y0 + ly, D.ny) * D.pitch + wrapm(x0 + lx, D.nx);
-        const int cx = a < N1 ? a % W1 - 1 : 0, cy = a < N1 ? a / W1 - 1 : 0;
-        oC[r] = wrapm(y0 + cy, D.ny) * D.pitch + wrapm(x0 + cx, D.nx);
     }
-    const int dlx = tid % TX, dly = tid / TX;
-    const int oD = wrapm(y0 + dly, D.ny) * D.pitch + wrapm(x0 + dlx, D.nx);
-    const bool own_xy = tid < NI && x0 + dlx < D.nx && y0 + dly < D.ny;
+    // this thread's node on the ring of tile + 1 around the tile (tid < NB),
+    // where stage B computes F and u only
+    int rx = 0, ry = 0;
+    if (tid < NB) {
+        if (tid < W1) { rx = tid - 1; ry = -1; }
+        else if (tid < 2 * W1) { rx = tid - W1 - 1; ry = TY; }
+        else if (tid < 2 * W1 + TY) { rx = -1; ry = tid - 2 * W1; }
+        else { rx = TX; ry = tid - 2 * W1 - TY; }
+    }
+    // the tile node this thread takes in stages B (F, u and the collision)
+    // and C; its wrapped neighbour offsets for the pushes
+    const int cx = tid % TX, cy = tid / TX;
+    const int gxo = x0 + cx, gyo = y0 + cy;
+    const bool own_xy = tid < NI && gxo < D.nx && gyo < D.ny;
+    const int oC = own_xy ? gyo * D.pitch + gxo : 0;
+    const long long oxp = own_xy && gxo == D.nx - 1 ? -(long long)(D.nx - 1) : 1;
+    const long long oxm = own_xy && gxo == 0 ? (long long)(D.nx - 1) : -1;
+    const long long oyp = own_xy && gyo == D.ny - 1 ? -(long long)(D.ny - 1) * D.pitch : D.pitch;
+    const long long oym = own_xy && gyo == 0 ? (long long)(D.ny - 1) * D.pitch : -(long long)D.pitch;
+    auto inplane = [&](int qxv, int qyv) {
+        return (qxv > 0 ? oxp : (qxv < 0 ? oxm : 0)) + (qyv > 0 ? oyp : (qyv < 0 ? oym : 0));
+    };
     int err = 0;
     double msum = 0.0;
 
-    for (int k = z0 - 3; k <= z1 + 3; ++k) {
-        // ================= phase 1: A(k), D5(k - 4)
-        if (k <= z1 + 2) {
-            R* const psA = s_psi + ring(k, 3) * N3;
+    for (int k = z0 - 2; k <= z1 + 2; ++k) {
+        // ================= phase 1: A(k), C(k - 3)
+        if (k <= z1 + 1) {
+            R* const psA = s_psi + ring(k, 3) * N2;
             if (D.walls && (k < 0 || k >= D.nz)) {
                 if (k == -1 || k == D.nz) {
                     const R* gp = (const R*)D.ghost + (k < 0 ? (size_t)0 : ZS);
 #pragma unroll
                     for (int r = 0; r < 2; ++r)
-                        if (tid + r * NT < N3) psA[tid + r * NT] = gp[oA[r]];
+                        if (tid + r * NT < N2) psA[tid + r * NT] = gp[oA[r]];
                 }
             } else {
                 const size_t zo = (size_t)wrapm(k, D.nz) * ZS;
-                R* const rA = s_rho + ring(k, 3) * N3;
-                R* const jA = s_j + ring(k, 2) * 3 * N3;
-                R* const tA = s_tdp + ring(k, 3) * N3;
+                R* const rA = s_rho + ring(k, 4) * N2;
+                R* const iA = s_ic + ring(k, 5) * N2;
+                R* const jA = s_j + ring(k, 2) * 3 * N2;
+                R* const tA = s_tdp + ring(k, 4) * N2;
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
                     const int a = tid + r * NT;
-                    if (a < N3) {
+                    if (a < N2) {
                         const size_t n = zo + oA[r];
                         R f[19], g[7];
 #pragma unroll
@@ -779,25 +768,96 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
                         if (!(T == T) || !(rho == rho)) err |= ERR_NONFINITE;
                         psA[a] = f_sqrt(q2);
                         rA[a] = rho;
+                        iA[a] = R(1) / (rho * L.cv);
                         jA[a] = jx;
-                        jA[N3 + a] = jy;
-                        jA[2 * N3 + a] = jz;
+                        jA[N2 + a] = jy;
+                        jA[2 * N2 + a] = jz;
                         tA[a] = tdp;
                     }
                 }
             }
         }
         {
-            const int q = k - 4;
+            const int q = k - 3;
             if (q >= z0 && q < z1 && own_xy) {
-                const size_t n = (size_t)q * ZS + oD;
-                const R iC = s_ic[ring(q, 2) * NI + tid];
+                const size_t n = (size_t)q * ZS + oC;
+                const bool lo_wall = D.walls && q == 0, hi_wall = D.walls && q == D.nz - 1;
+                const R* const um = s_u + ring(q - 1, 3) * 3 * N1;
+                const R* const u0 = s_u + ring(q, 3) * 3 * N1;
+                const R* const up = s_u + ring(q + 1, 3) * 3 * N1;
+                const int c1 = (cy + 1) * W1 + cx + 1, c2 = (cy + 2) * W2 + cx + 2;
+                // div u: (1/c_s^2) sum_i w_i c_i . u(x + c_i); walls carry u = 0
+                R divu = 0;
 #pragma unroll
-                for (int i = 0; i < 7; ++i) {
-                    const R go = gc[i * PL + n];
-                    gnx[i * PL + n] = L.frozen_thermal
-                                          ? go
-                                          : go + (s_g[(gbase(i) + ring(q, gslots(i))) * NI + tid] - go) * iC;
+                for (int i = 1; i < 19; ++i) {
+                    if ((qz(i) < 0 && lo_wall) || (qz(i) > 0 && hi_wall)) continue;
+                    const R* us = (qz(i) < 0 ? um : (qz(i) > 0 ? up : u0)) + c1 + qy(i) * W1 + qx(i);
+                    R cu = 0;
+                    if (qx(i)) cu += R(qx(i)) * us[0];
+                    if (qy(i)) cu += R(qy(i)) * us[N1];
+                    if (qz(i)) cu += R(qz(i)) * us[2 * N1];
+                    divu += R(3.0 * qw(i)) * cu;
+                }
+                R g[7];
+#pragma unroll
+                for (int i = 0; i < 7; ++i) g[i] = gc[i * PL + n];
+                const R ux = u0[c1], uy = u0[N1 + c1], uz = u0[2 * N1 + c1];
+                const R rho = s_rho[ring(q, 4) * N2 + c2], TdpdT = s_tdp[ring(q, 4) * N2 + c2];
+                // grad T from the local first moments: c^_s^2 d_a T = -vs1 m^_a
+                const R m1 = g[1] - g[2], m2 = g[3] - g[4], m3 = g[5] - g[6];
+                const R kT = -L.vs1 / L.cs2h;
+                const R dTx = kT * m1, dTy = kT * m2, dTz = kT * m3;
+                const R C = rho * L.cv;
+                const R Q = -(C * (ux * dTx + uy * dTy + uz * dTz) + TdpdT * divu);
+                const R Pn = Q / C;
+                const R Qs = step == 0 ? Q : Q + R(0.5) * (Q - C * Pc[n]);
+                Pnx[n] = Pn;
+                // ---- D3Q7 MRT collision (deviation form), closed-form inverse
+                const R Td = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+                const R m4 = g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+                const R m5 = (g[1] + g[2]) - (g[3] + g[4]);
+                const R m6 = (g[3] + g[4]) - (g[5] + g[6]);
+                const R wd = L.w7_1 * R(6);
+                const R s0 = Td - L.vs0 * (Td - Td) + Qs;
+                const R s1 = m1 - L.vs1 * m1, s2 = m2 - L.vs1 * m2, s3 = m3 - L.vs1 * m3;
+                const R s4 = m4 - L.vs3 * (m4 - wd * Td) + wd * Qs;
+                const R s5 = m5 - L.vs4 * m5, s6 = m6 - L.vs4 * m6;
+                const R bq = (s4 - s5 + s6) * R(1.0 / 3.0);
+                const R aq = bq + s5, cq = bq - s6;
+                R gs[7];
+                gs[0] = s0 - s4;
+                gs[1] = R(0.5) * (aq + s1);
+                gs[2] = R(0.5) * (aq - s1);
+                gs[3] = R(0.5) * (bq + s2);
+                gs[4] = R(0.5) * (bq - s2);
+                gs[5] = R(0.5) * (cq + s3);
+                gs[6] = R(0.5) * (cq - s3);
+                // weighted streaming (Eq. 39) from this node's side: g*_i lands on
+                // x = y + c_i as g_i(x) + (g*_i - g_i(x)) / (rho(x) c_v) of the
+                // current state; through a wall it returns here as the opposite
+                // direction, A = 2 w^ T_w - g*_i (Dirichlet) or g*_i (adiabatic)
+                if (L.frozen_thermal) {
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) gnx[i * PL + n] = g[i];
+                } else {
+                    const long long zp = q == D.nz - 1 ? -(long long)(D.nz - 1) * (long long)ZS : (long long)ZS;
+                    const long long zm = q == 0 ? (long long)(D.nz - 1) * (long long)ZS : -(long long)ZS;
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) {
+                        if ((i == 5 && hi_wall) || (i == 6 && lo_wall)) {
+                            const int e = i == 5 ? 1 : 0, o = i == 5 ? 6 : 5;
+                            const R Ai = D.therm[e] == T_DIRICHLET
+                                             ? R(2) * L.w7_1 * (R)(D.T_edge[e] - D.T_ref) - gs[i]
+                                             : gs[i];
+                            gnx[o * PL + n] = g[o] + (Ai - g[o]) * s_ic[ring(q, 5) * N2 + c2];
+                        } else {
+                            const long long off = inplane(hx(i), hy(i)) + (hz(i) > 0 ? zp : (hz(i) < 0 ? zm : 0));
+                            const size_t m = (size_t)((long long)n + off);
+                            const R go = gc[i * PL + m];
+                            const R iCm = s_ic[ring(q + hz(i), 5) * N2 + c2 + hy(i) * W2 + hx(i)];
+                            gnx[i * PL + m] = go + (gs[i] - go) * iCm;
+                        }
+                    }
                 }
             }
         }
@@ -806,54 +866,62 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
         // ================= phase 2: B(k - 1)
         {
             const int p = k - 1;
-            if (p >= z0 - 2 && p <= z1 + 1 && !(D.walls && (p < 0 || p >= D.nz))) {
-                // f* is needed from planes z0 - 1 .. z1 only
-                const bool coll = !L.frozen_flow && p >= z0 - 1 && p <= z1;
-                const size_t zo = (size_t)wrapm(p, D.nz) * ZS;
-                const R* const psm = s_psi + ring(p - 1, 3) * N3;
-                const R* const ps0 = s_psi + ring(p, 3) * N3;
-                const R* const psp = s_psi + ring(p + 1, 3) * N3;
-                const R* const rB = s_rho + ring(p, 3) * N3;
-                const R* const jB = s_j + ring(p, 2) * 3 * N3;
-                R* const uB = s_u + ring(p, 3) * 3 * N2;
+            if (p >= z0 - 1 && p <= z1 && !(D.walls && (p < 0 || p >= D.nz))) {
+                const bool own_z = p >= z0 && p < z1;
+                const R* const psm = s_psi + ring(p - 1, 3) * N2;
+                const R* const ps0 = s_psi + ring(p, 3) * N2;
+                const R* const psp = s_psi + ring(p + 1, 3) * N2;
+                const R* const rB = s_rho + ring(p, 4) * N2;
+                const R* const jB = s_j + ring(p, 2) * 3 * N2;
+                R* const uB = s_u + ring(p, 3) * 3 * N1;
+                // pass 0: this thread's ring node of tile + 1; pass 1: its tile node
 #pragma unroll 1
                 for (int r = 0; r < 2; ++r) {
-                    const int b = tid + r * NT;
-                    if (b >= N2) break;
-                    // (selects, not indexing: the arrays stay in registers)
-                    const int lx = r ? bx[1] : bx[0], ly = r ? by[1] : by[0];
-                    const int c3 = (ly + 3) * W3 + lx + 3;
+                    if (r == 0 ? tid >= NB : tid >= NI) continue;
+                    const int lx = r ? cx : rx, ly = r ? cy : ry;
+                    const int c2 = (ly + 2) * W2 + lx + 2;
                     R sx = 0, sy = 0, sz = 0;
 #pragma unroll
                     for (int i = 1; i < 19; ++i) {
                         const R* pp = qz(i) < 0 ? psm : (qz(i) > 0 ? psp : ps0);
-                        const R pn = pp[c3 + qy(i) * W3 + qx(i)];
+                        const R pn = pp[c2 + qy(i) * W2 + qx(i)];
                         const R wv = qc2(i) == 1 ? R(1.0 / 6.0) : R(1.0 / 12.0);
                         if (qx(i)) sx += wv * pn * R(qx(i));
                         if (qy(i)) sy += wv * pn * R(qy(i));
                         if (qz(i)) sz += wv * pn * R(qz(i));
                     }
-                    const R psi = ps0[c3], rho = rB[c3];
+                    const R psi = ps0[c2], rho = rB[c2];
                     const R Fx = P.negG * psi * sx, Fy = P.negG * psi * sy;
                     const R Fz = P.negG * psi * sz - L.gravity * (rho - rho_ave);
                     R ux = 0, uy = 0, uz = 0;
                     if (!L.frozen_flow) {
                         const R ir = R(1) / rho;
-                        ux = (jB[c3] + R(0.5) * Fx) * ir;
-                        uy = (jB[N3 + c3] + R(0.5) * Fy) * ir;
-                        uz = (jB[2 * N3 + c3] + R(0.5) * Fz) * ir;
+                        ux = (jB[c2] + R(0.5) * Fx) * ir;
+                        uy = (jB[N2 + c2] + R(0.5) * Fy) * ir;
+                        uz = (jB[2 * N2 + c2] + R(0.5) * Fz) * ir;
                     }
-                    const int c2 = (ly + 2) * W2 + lx + 2;
-                    uB[c2] = ux;
-                    uB[N2 + c2] = uy;
-                    uB[2 * N2 + c2] = uz;
-                    if (!coll || b < NB) continue;
-                    // ---- D3Q19 MRT collision in moment space
-                    const R Fm2 = P.negG * P.negG * (sx * sx + sy * sy + sz * sz);
-                    const size_t n = zo + (r ? oB[1] : oB[0]);
+                    const int c1 = (ly + 1) * W1 + lx + 1;
+                    uB[c1] = ux;
+                    uB[N1 + c1] = uy;
+                    uB[2 * N1 + c1] = uz;
+                    // the tile node: collide it if this CTA owns it
+                    if (r == 0 || !own_z || !own_xy) continue;
+                    const size_t n = (size_t)p * ZS + oC;
                     R f[19];
 #pragma unroll
                     for (int i = 0; i < 19; ++i) f[i] = fc[i * PL + n];
+                    if (L.frozen_flow) {
+                        R rd = 0;
+#pragma unroll
+                        for (int i = 0; i < 19; ++i) {
+                            fnx[i * PL + n] = f[i];
+                            rd += f[i];
+                        }
+                        if (use_mass) msum += (double)(rd + rho_ref);
+                        continue;
+                    }
+                    // ---- D3Q19 MRT collision in moment space
+                    const R Fm2 = P.negG * P.negG * (sx * sx + sy * sy + sz * sz);
                     R m[19];
                     moments19(f, m);
                     m[0] += rho_ref;
@@ -889,137 +957,24 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
                         dm[kk] = (-sk[kk] * (m[kk] - meq[kk]) + (R(1) - R(0.5) * sk[kk]) * Fb[kk]) *
                                  R(1.0 / mnorm(kk));
                     add_inverse19(dm, f);   // f* = f + M^T dm
-                    const bool in_tile = lx >= 0 && lx < TX && ly >= 0 && ly < TY;
-                    static_for<19>([&](auto ic) {
-                        constexpr int i = decltype(ic)::value;
-                        const R v = f[i];
-                        const int dz = p + qz(i);
-                        if (D.walls && (dz < 0 || dz >= D.nz)) {
-                            // halfway bounce-back: f_opp(i)(x, t+1) = f*_i(x)
-                            if (in_tile)
-                                s_f[(fbase(qopp(i)) + ring(p, fslots(qopp(i)))) * NI + ly * TX + lx] = v;
+                    // push to x + c_i; through a wall f*_i returns as f_opp(i)
+                    const long long zp = p == D.nz - 1 ? -(long long)(D.nz - 1) * (long long)ZS : (long long)ZS;
+                    const long long zm = p == 0 ? (long long)(D.nz - 1) * (long long)ZS : -(long long)ZS;
+                    const bool lo_wall = D.walls && p == 0, hi_wall = D.walls && p == D.nz - 1;
+                    R rd = 0;
+                    static_for<19>([&](auto icn) {
+                        constexpr int i = decltype(icn)::value;
+                        rd += f[i];
+                        if ((qz(i) < 0 && lo_wall) || (qz(i) > 0 && hi_wall)) {
+                            fnx[qopp(i) * PL + n] = f[i];
                         } else {
-                            const int dx = lx + qx(i), dy = ly + qy(i);
-                            if (dx >= 0 && dx < TX && dy >= 0 && dy < TY)
-                                s_f[(fbase(i) + ring(dz, fslots(i))) * NI + dy * TX + dx] = v;
+                            const long long off = inplane(qx(i), qy(i)) + (qz(i) > 0 ? zp : (qz(i) < 0 ? zm : 0));
+                            fnx[i * PL + (size_t)((long long)n + off)] = f[i];
                         }
                     });
+                    // the new state's mass: streaming moves the f* without loss
+                    if (use_mass) msum += (double)(rd + rho_ref);
                 }
-            }
-        }
-        __syncthreads();
-
-        // ================= phase 3: C(k - 2), D9(k - 2)
-        {
-            const int q = k - 2;
-            if (q >= z0 - 1 && q <= z1 && !(D.walls && (q < 0 || q >= D.nz))) {
-                const size_t zo = (size_t)wrapm(q, D.nz) * ZS;
-                const bool own_z = q >= z0 && q < z1;
-                const bool lo_wall = D.walls && q == 0, hi_wall = D.walls && q == D.nz - 1;
-                const R* const um = s_u + ring(q - 1, 3) * 3 * N2;
-                const R* const u0 = s_u + ring(q, 3) * 3 * N2;
-                const R* const up = s_u + ring(q + 1, 3) * 3 * N2;
-                const R* const rC = s_rho + ring(q, 3) * N3;
-                const R* const tC = s_tdp + ring(q, 3) * N3;
-#pragma unroll 1
-                for (int r = 0; r < 2; ++r) {
-                    const int c = tid + r * NT;
-                    if (c >= N1) break;
-                    const int lx = c % W1 - 1, ly = c / W1 - 1;
-                    const int c2 = (ly + 2) * W2 + lx + 2, c3 = (ly + 3) * W3 + lx + 3;
-                    // div u: (1/c_s^2) sum_i w_i c_i . u(x + c_i); walls carry u = 0
-                    R divu = 0;
-#pragma unroll
-                    for (int i = 1; i < 19; ++i) {
-                        if ((qz(i) < 0 && lo_wall) || (qz(i) > 0 && hi_wall)) continue;
-                        const R* us = (qz(i) < 0 ? um : (qz(i) > 0 ? up : u0)) + c2 + qy(i) * W2 + qx(i);
-                        R cu = 0;
-                        if (qx(i)) cu += R(qx(i)) * us[0];
-                        if (qy(i)) cu += R(qy(i)) * us[N2];
-                        if (qz(i)) cu += R(qz(i)) * us[2 * N2];
-                        divu += R(3.0 * qw(i)) * cu;
-                    }
-                    const size_t n = zo + (r ? oC[1] : oC[0]);
-                    R g[7];
-#pragma unroll
-                    for (int i = 0; i < 7; ++i) g[i] = gc[i * PL + n];
-                    const R ux = u0[c2], uy = u0[N2 + c2], uz = u0[2 * N2 + c2];
-                    const R rho = rC[c3], TdpdT = tC[c3];
-                    // grad T from the local first moments: c^_s^2 d_a T = -vs1 m^_a
-                    const R m1 = g[1] - g[2], m2 = g[3] - g[4], m3 = g[5] - g[6];
-                    const R kT = -L.vs1 / L.cs2h;
-                    const R dTx = kT * m1, dTy = kT * m2, dTz = kT * m3;
-                    const R C = rho * L.cv;
-                    const R Q = -(C * (ux * dTx + uy * dTy + uz * dTz) + TdpdT * divu);
-                    const R Pn = Q / C;
-                    const R Qs = step == 0 ? Q : Q + R(0.5) * (Q - C * Pc[n]);
-                    const bool in_tile = lx >= 0 && lx < TX && ly >= 0 && ly < TY;
-                    const int ti = ly * TX + lx;
-                    if (in_tile) {
-                        if (own_z && x0 + lx < D.nx && y0 + ly < D.ny) Pnx[n] = Pn;
-                        s_ic[ring(q, 2) * NI + ti] = R(1) / (rho * L.cv);
-                    }
-                    // ---- D3Q7 MRT collision (deviation form), closed-form inverse
-                    const R Td = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
-                    const R m4 = g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
-                    const R m5 = (g[1] + g[2]) - (g[3] + g[4]);
-                    const R m6 = (g[3] + g[4]) - (g[5] + g[6]);
-                    const R wd = L.w7_1 * R(6);
-                    const R s0 = Td - L.vs0 * (Td - Td) + Qs;
-                    const R s1 = m1 - L.vs1 * m1, s2 = m2 - L.vs1 * m2, s3 = m3 - L.vs1 * m3;
-                    const R s4 = m4 - L.vs3 * (m4 - wd * Td) + wd * Qs;
-                    const R s5 = m5 - L.vs4 * m5, s6 = m6 - L.vs4 * m6;
-                    const R bq = (s4 - s5 + s6) * R(1.0 / 3.0);
-                    const R aq = bq + s5, cq = bq - s6;
-                    R gs[7];
-                    gs[0] = s0 - s4;
-                    gs[1] = R(0.5) * (aq + s1);
-                    gs[2] = R(0.5) * (aq - s1);
-                    gs[3] = R(0.5) * (bq + s2);
-                    gs[4] = R(0.5) * (bq - s2);
-                    gs[5] = R(0.5) * (cq + s3);
-                    gs[6] = R(0.5) * (cq - s3);
-                    // in-plane directions land in this plane
-#pragma unroll
-                    for (int i = 0; i < 5; ++i) {
-                        const int dx = lx + hx(i), dy = ly + hy(i);
-                        if (dx >= 0 && dx < TX && dy >= 0 && dy < TY)
-                            s_g[(gbase(i) + ring(q, 2)) * NI + dy * TX + dx] = gs[i];
-                    }
-                    if (in_tile) {
-                        // +z lands on the plane above; at the top wall it returns
-                        // as -z: A = 2 w^ T_w - g*_5 (Dirichlet) or g*_5 (adiabatic)
-                        if (hi_wall)
-                            s_g[(gbase(6) + ring(q, 2)) * NI + ti] =
-                                D.therm[1] == T_DIRICHLET
-                                    ? R(2) * L.w7_1 * (R)(D.T_edge[1] - D.T_ref) - gs[5]
-                                    : gs[5];
-                        else
-                            s_g[(gbase(5) + ring(q + 1, 3)) * NI + ti] = gs[5];
-                        if (lo_wall)
-                            s_g[(gbase(5) + ring(q, 3)) * NI + ti] =
-                                D.therm[0] == T_DIRICHLET
-                                    ? R(2) * L.w7_1 * (R)(D.T_edge[0] - D.T_ref) - gs[6]
-                                    : gs[6];
-                        else
-                            s_g[(gbase(6) + ring(q - 1, 2)) * NI + ti] = gs[6];
-                    }
-                }
-            }
-        }
-        {
-            const int q = k - 2;
-            if (q >= z0 && q < z1 && own_xy) {
-                const size_t n = (size_t)q * ZS + oD;
-                R rd = 0;
-#pragma unroll
-                for (int i = 0; i < 19; ++i) {
-                    const R v = L.frozen_flow ? fc[i * PL + n]
-                                              : s_f[(fbase(i) + ring(q, fslots(i))) * NI + tid];
-                    fnx[i * PL + n] = v;
-                    rd += v;
-                }
-                if (use_mass) msum += (double)(rd + rho_ref);
             }
         }
         __syncthreads();
@@ -1143,7 +1098,7 @@ struct lbm3d_ctx {
     Ctl* ctl = nullptr;
     Dom3 D;
     cudaGraphExec_t graph = nullptr;
-    bool fused = false;      // one fused kernel per step (else three kernels)
+    bool fused = true;       // one fused kernel per step (else three kernels)
     int zseg = 0;            // planes per CTA of the fused step
     bool aux_stale = false;  // the per-node planes lag the state (fused steps)
     long long step = 0;
@@ -1168,7 +1123,7 @@ size_t bytes_for(int nx, int ny, int nz, int prec) {
 }
 
 // planes per CTA of the fused step: enough (tile, segment) units for about
-// four per resident CTA, segments of at least 16 planes
+// three per resident CTA, segments of 16 to 48 planes
 int auto_zseg(int nx, int ny, int nz, int prec) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1178,9 +1133,10 @@ int auto_zseg(int nx, int ny, int nz, int prec) {
     const long long tiles = (long long)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
     const long long slots = (long long)sms * (prec == LBM_FP64 ? Tile3<double>::MIN_BLOCKS
                                                               : Tile3<float>::MIN_BLOCKS);
-    const long long nseg = (4 * slots + tiles - 1) / tiles;
+    const long long nseg = (3 * slots + tiles - 1) / tiles;
     int zs = (int)((nz + nseg - 1) / nseg);
     if (zs < 16) zs = 16;
+    if (zs > 48) zs = 48;
     return zs > nz ? nz : zs;
 }
 
@@ -1357,6 +1313,9 @@ int lbm3d_create(int nx, int ny, int nz, const lbm_params* params, const lbm3d_b
     D.T_ref = 0.0;
     D.inv_n = 1.0 / ((double)nx * ny * nz);
     c->zseg = auto_zseg(nx, ny, nz, prec);
+    // the fused step is the faster in FP32; in FP64 (bound by the FP64 pipe)
+    // its recomputed halos cost more than the traffic it saves
+    c->fused = prec == LBM_FP32;
     if (prec == LBM_FP64)
         e = cudaFuncSetAttribute(k3_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Tile3<double>::BYTES);
