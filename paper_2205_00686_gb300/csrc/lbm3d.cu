@@ -3,8 +3,11 @@
 // energy moment) + D3Q7 temperature lattice with the rho c_v-weighted
 // streaming of Eq. 39, x and y periodic, z periodic or walls.
 //
-// The default step is three kernels over the nodes (plus a one-thread
-// counter update), because every stage needs neighbours of the previous one:
+// Two forms of the step give the same result.  k3_fused (below; the default
+// in FP32) does the whole step in one kernel over z-marching tiles.  The other
+// form (the default in FP64) is three kernels over the nodes plus a
+// one-thread counter update, because every stage needs neighbours of the
+// previous one:
 //   k3_force    psi of the 18 neighbours (ghost layer at walls) -> F_m, F,
 //               u = (j + F/2)/rho, |F_m|^2/psi^2                (Eqs. 9, 11)
 //   k3_collide  div u (neighbour u), grad T (local moments), Q, P^n, S;
@@ -17,7 +20,6 @@
 // Per node and step (FP32) this moves about 1.9 times the 216 B of one read
 // and one write of the state: f is read again after the push to build the
 // next state's fields, and u, F and the per-node fields pass through memory.
-// k3_fused (below) does the whole step in one kernel with recomputed halos.
 //
 // Populations are stored as deviations f_i - w_i rho_ref and g_i - w^_i T_ref.
 // Planes are [q][nz][ny][pitch], 64-bit offsets.
