@@ -270,7 +270,7 @@ def served_check(n_inst, steps, budget_gb=1.0):
     cases = W.batch_instances(n_inst, steps=steps)
     gaps = -np.log(1.0 - W.uniform(77, n_inst)) * 0.002       # mean 2 ms between arrivals
     arrivals = [(float(t), c, steps) for t, c in zip(np.cumsum(gaps), cases)]
-    be = CudaBackend("fp32", autotune_steps=3)
+    be = CudaBackend("fp32", autotune_steps=3, autotune_at=32)
     srv = Server(be, mem_budget=int(budget_gb * 2 ** 30), chunk=100)
     st = srv.run(arrivals)
     nodes = sum(c.nx * c.ny for c in cases)

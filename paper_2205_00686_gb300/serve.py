@@ -68,7 +68,8 @@ class CudaBackend:
     two streams (no host wait), so a domain can be initialised, or read back
     after it left the batch, while the next chunk of steps runs."""
 
-    def __init__(self, prec: str = "fp32", stream=None, autotune_steps: int = 0):
+    def __init__(self, prec: str = "fp32", stream=None, autotune_steps: int = 0,
+                 autotune_at: int = 1):
         import torch
 
         import paper_2205_00686_gb300 as lbm
@@ -81,8 +82,11 @@ class CudaBackend:
         self.attached: Dict[int, bool] = {}
         # with autotune_steps > 0, a batch's tile is chosen by
         # lbm_batch_autotune (trials of that many steps on a shadow batch of
-        # its members' shapes) before its first chunk, and kept after
+        # its members' shapes) before the first chunk in which it holds at
+        # least autotune_at domains, and kept after: tuned on the first
+        # arrival alone, a batch keeps a tile made for one small domain
         self.autotune_steps = int(autotune_steps)
+        self.autotune_at = max(1, int(autotune_at))
         self.tuned = set()
 
     def bytes_for(self, case) -> int:
@@ -125,7 +129,7 @@ class CudaBackend:
         for key, b in self.batches.items():
             if not len(b):
                 continue
-            if self.autotune_steps and key not in self.tuned:
+            if self.autotune_steps and key not in self.tuned and len(b) >= self.autotune_at:
                 b.autotune(self.autotune_steps)
                 self.tuned.add(key)
             b.step(n)
