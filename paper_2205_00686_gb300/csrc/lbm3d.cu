@@ -640,7 +640,6 @@ __global__ void k3_advance(Ctl* ctl, double qscale) {
 // ring slot of plane k (k >= -8)
 __device__ __forceinline__ int ring(int k, int s) { return (k + 24) % s; }
 
-
 #ifndef K3_TILE_X
 #define K3_TILE_X 16
 #define K3_TILE_Y 16
