@@ -21,6 +21,8 @@
 // and one write of the state: f is read again after the push to build the
 // next state's fields, and u, F and the per-node fields pass through memory.
 //
+// Reciprocals use f_rcp as in two dimensions (the hardware approximation in
+// FP32; Newton-Raphson from it, within about one ulp, in FP64).
 // Populations are stored as deviations f_i - w_i rho_ref and g_i - w^_i T_ref.
 // Planes are [q][nz][ny][pitch], 64-bit offsets.
 #include <math.h>
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(128) k3_force(Dom3 D, Phys<R> P, Lat3<R> L) {
     force_at<R>(D, P, L, x, y, z, n, nb, __ldcg(&D.ctl->step), &err, F, &Fm2);
     R ux = 0, uy = 0, uz = 0;
     if (!L.frozen_flow) {
-        const R ir = R(1) / A[A_RHO * D.plane + n];
+        const R ir = f_rcp(A[A_RHO * D.plane + n]);
         ux = (A[A_JX * D.plane + n] + R(0.5) * F[0]) * ir;
         uy = (A[A_JY * D.plane + n] + R(0.5) * F[1]) * ir;
         uz = (A[A_JZ * D.plane + n] + R(0.5) * F[2]) * ir;
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(128) k3_collide(Dom3 D, Phys<R> P, Lat3<R> L) 
     const R dTx = k * m1, dTy = k * m2, dTz = k * m3;
     const R C = rho * L.cv;
     const R Q = -(C * (ux * dTx + uy * dTy + uz * dTz) + TdpdT * divu);
-    const R Pn = Q / C;
+    const R Pn = Q * f_rcp(C);
     const R Qs = step == 0 ? Q : Q + R(0.5) * (Q - C * Pc[n]);
 
     // ---- D3Q19 MRT collision in moment space
@@ -557,7 +559,7 @@ __device__ __forceinline__ void macro_node(const Dom3& D, const Phys<R>& P, R cv
     A[A_T * D.plane + n] = T;
     A[A_PSI * D.plane + n] = f_sqrt(q2);
     A[A_TDPDT * D.plane + n] = TdpdT;
-    A[A_IC * D.plane + n] = R(1) / (rho * cv);
+    A[A_IC * D.plane + n] = f_rcp(rho * cv);
     A[A_JX * D.plane + n] = jx;
     A[A_JY * D.plane + n] = jy;
     A[A_JZ * D.plane + n] = jz;
@@ -770,7 +772,7 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
                         if (!(T == T) || !(rho == rho)) err |= ERR_NONFINITE;
                         psA[a] = f_sqrt(q2);
                         rA[a] = rho;
-                        iA[a] = R(1) / (rho * L.cv);
+                        iA[a] = f_rcp(rho * L.cv);
                         jA[a] = jx;
                         jA[N2 + a] = jy;
                         jA[2 * N2 + a] = jz;
@@ -811,7 +813,7 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
                 const R dTx = kT * m1, dTy = kT * m2, dTz = kT * m3;
                 const R C = rho * L.cv;
                 const R Q = -(C * (ux * dTx + uy * dTy + uz * dTz) + TdpdT * divu);
-                const R Pn = Q / C;
+                const R Pn = Q * f_rcp(C);
                 const R Qs = step == 0 ? Q : Q + R(0.5) * (Q - C * Pc[n]);
                 Pnx[n] = Pn;
                 // ---- D3Q7 MRT collision (deviation form), closed-form inverse
@@ -897,7 +899,7 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
                     const R Fz = P.negG * psi * sz - L.gravity * (rho - rho_ave);
                     R ux = 0, uy = 0, uz = 0;
                     if (!L.frozen_flow) {
-                        const R ir = R(1) / rho;
+                        const R ir = f_rcp(rho);
                         ux = (jB[c2] + R(0.5) * Fx) * ir;
                         uy = (jB[N2 + c2] + R(0.5) * Fy) * ir;
                         uz = (jB[2 * N2 + c2] + R(0.5) * Fz) * ir;
