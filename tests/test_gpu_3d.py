@@ -241,3 +241,44 @@ def test_fused_fp32_equals_itself_for_any_segment_length():
     for other in out[1:]:
         for a, b in zip(out[0], other):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "three_kernels"])
+@pytest.mark.parametrize("shape", [(20, 1, 1), (1, 18, 1), (1, 1, 24), (12, 9, 1), (1, 7, 11)])
+def test_thin_domains_match_oracle(shape, fused):
+    """Domains one node thick along one or two axes (every neighbour along
+    those axes is the node itself, and a 16 x 16 tile wraps many times onto
+    the domain): a uniform vapour-like state with density and temperature
+    noise and a small velocity, periodic, FP64 against the oracle after 20
+    steps."""
+    import paper_2205_00686_gb300 as lbm
+    nx, ny, nz = shape
+    p = W.params()
+    sh = (nz, ny, nx)
+    rho = 0.3 * (1.0 + W.noise(3, sh, 1e-3))
+    T = 0.95 * W.TC * (1.0 + W.noise(4, sh, 1e-3))
+    u = [W.noise(5 + i, sh, 1e-3) for i in range(3)]
+    o = O.Sim3(nx, ny, nz, p, W.periodic_bc3())
+    o.init(rho, *u, T)
+    o.step(20)
+    d = lbm.Domain3(nx, ny, nz, p, W.periodic_bc3(), prec="fp64")
+    d.set_path(fused, 0)
+    d.init_fields(rho, *u, T)
+    d.step(20)
+    e = fields_err(d, o)
+    assert max(e.values()) <= 1e-10, e
+    gf, gg, gP = d.populations()
+    of, og, oP = o.populations()
+    assert P.rel_err(gf, of) <= 1e-12 and P.rel_err(gg, og) <= 1e-12
+    d.close()
+
+
+def test_set_path_refuses_a_negative_segment():
+    import paper_2205_00686_gb300 as lbm
+    c = cases()["periodic"]
+    d = lbm.Domain3(c.nx, c.ny, c.nz, c.params, c.bc, prec="fp32")
+    with pytest.raises(lbm.LbmError):
+        d.set_path(True, -1)
+    d.set_path(True, 10 ** 6)            # clamped to the domain's planes
+    assert d.path == (True, c.nz)
+    d.close()
