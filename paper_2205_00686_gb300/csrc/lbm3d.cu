@@ -727,8 +727,9 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
     };
     int err = 0;
     double msum = 0.0;
+    int kzA = wrapm(z0 - 2, D.nz);   // the plane of A(k), wrapped; advanced with k
 
-    for (int k = z0 - 2; k <= z1 + 2; ++k) {
+    for (int k = z0 - 2; k <= z1 + 2; ++k, kzA = kzA + 1 == D.nz ? 0 : kzA + 1) {
         // ================= phase 1: A(k), C(k - 3)
         if (k <= z1 + 1) {
             R* const psA = s_psi + ring(k, 3) * N2;
@@ -740,7 +741,7 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
                         if (tid + r * NT < N2) psA[tid + r * NT] = gp[oA[r]];
                 }
             } else {
-                const size_t zo = (size_t)wrapm(k, D.nz) * ZS;
+                const size_t zo = (size_t)kzA * ZS;
                 R* const rA = s_rho + ring(k, 4) * N2;
                 R* const iA = s_ic + ring(k, 5) * N2;
                 R* const jA = s_j + ring(k, 2) * 3 * N2;
@@ -791,17 +792,18 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
                 const R* const up = s_u + ring(q + 1, 3) * 3 * N1;
                 const int c1 = (cy + 1) * W1 + cx + 1, c2 = (cy + 2) * W2 + cx + 2;
                 // div u: (1/c_s^2) sum_i w_i c_i . u(x + c_i); walls carry u = 0
-                R divu = 0;
+                // (3 w_i = 1/6 on the axes, 1/12 on the diagonals, summed apart)
+                R dva = 0, dvd = 0;
 #pragma unroll
                 for (int i = 1; i < 19; ++i) {
                     if ((qz(i) < 0 && lo_wall) || (qz(i) > 0 && hi_wall)) continue;
                     const R* us = (qz(i) < 0 ? um : (qz(i) > 0 ? up : u0)) + c1 + qy(i) * W1 + qx(i);
-                    R cu = 0;
-                    if (qx(i)) cu += R(qx(i)) * us[0];
-                    if (qy(i)) cu += R(qy(i)) * us[N1];
-                    if (qz(i)) cu += R(qz(i)) * us[2 * N1];
-                    divu += R(3.0 * qw(i)) * cu;
+                    R& acc = qc2(i) == 1 ? dva : dvd;
+                    if (qx(i)) acc += R(qx(i)) * us[0];
+                    if (qy(i)) acc += R(qy(i)) * us[N1];
+                    if (qz(i)) acc += R(qz(i)) * us[2 * N1];
                 }
+                const R divu = dva * R(1.0 / 6.0) + dvd * R(1.0 / 12.0);
                 R g[7];
 #pragma unroll
                 for (int i = 0; i < 7; ++i) g[i] = gc[i * PL + n];
@@ -884,16 +886,26 @@ k3_fused(Dom3 D, Phys<R> P, Lat3<R> L, int zseg, int use_mass) {
                     if (r == 0 ? tid >= NB : tid >= NI) continue;
                     const int lx = r ? cx : rx, ly = r ? cy : ry;
                     const int c2 = (ly + 2) * W2 + lx + 2;
-                    R sx = 0, sy = 0, sz = 0;
+                    // sum_i varpi(|c_i|^2) psi(x + c_i) c_i with the axis (1/6) and
+                    // diagonal (1/12) neighbours summed apart and weighted once
+                    R ax = 0, ay = 0, az = 0, dx = 0, dy = 0, dz = 0;
 #pragma unroll
                     for (int i = 1; i < 19; ++i) {
                         const R* pp = qz(i) < 0 ? psm : (qz(i) > 0 ? psp : ps0);
                         const R pn = pp[c2 + qy(i) * W2 + qx(i)];
-                        const R wv = qc2(i) == 1 ? R(1.0 / 6.0) : R(1.0 / 12.0);
-                        if (qx(i)) sx += wv * pn * R(qx(i));
-                        if (qy(i)) sy += wv * pn * R(qy(i));
-                        if (qz(i)) sz += wv * pn * R(qz(i));
+                        if (qc2(i) == 1) {
+                            if (qx(i)) ax += R(qx(i)) * pn;
+                            if (qy(i)) ay += R(qy(i)) * pn;
+                            if (qz(i)) az += R(qz(i)) * pn;
+                        } else {
+                            if (qx(i)) dx += R(qx(i)) * pn;
+                            if (qy(i)) dy += R(qy(i)) * pn;
+                            if (qz(i)) dz += R(qz(i)) * pn;
+                        }
                     }
+                    const R sx = ax * R(1.0 / 6.0) + dx * R(1.0 / 12.0);
+                    const R sy = ay * R(1.0 / 6.0) + dy * R(1.0 / 12.0);
+                    const R sz = az * R(1.0 / 6.0) + dz * R(1.0 / 12.0);
                     const R psi = ps0[c2], rho = rB[c2];
                     const R Fx = P.negG * psi * sx, Fy = P.negG * psi * sy;
                     const R Fz = P.negG * psi * sz - L.gravity * (rho - rho_ave);
