@@ -658,7 +658,8 @@ struct Tile3 {
     static constexpr int ELEMS = 22 * N2 + 9 * N1;
     static constexpr size_t BYTES = (size_t)ELEMS * sizeof(R);
     // FP32: three CTAs per SM (80 registers, no spills; 11.7 against 10.1
-    // GLUPS with two at 120 registers; four spill); FP64 needs ~240 registers
+    // GLUPS with two at 120 registers, against 10.2 with four, which spill);
+    // FP64 needs ~240 registers
     static constexpr int MIN_BLOCKS = (sizeof(R) == 4 && NT <= 256) ? 3 : 1;
     static_assert(NI <= NT, "the collisions take one tile node per thread");
     static_assert(N2 <= 2 * NT && N1 <= 2 * NT, "two passes per stage");
