@@ -513,6 +513,12 @@ def run_ours(args):
               for a in case.fields()]
     outs = [torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
     e2e_steps = args.steps
+    # one untimed pass of the same calls first (the first transfers to and
+    # from freshly pinned buffers pay one-off mapping costs, and the step's
+    # graph is captured), as the device timing has its warm-up steps
+    dom.init_fields(*pinned)
+    dom.step(max(args.warmup, 1))
+    dom.get_rho_u_T(tuple(outs))
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -526,7 +532,8 @@ def run_ours(args):
     e2e = {"value": round(job_mlups(world, N, e2e_steps, te), 1), "unit": "MLUPS",
            "h2d_bytes_per_step": int(4 * N * 8 / e2e_steps),
            "d2h_bytes_per_step": int(4 * N * 8 / e2e_steps),
-           "call": "lbm_init_fields(host) + lbm_step(%d) + lbm_get_rho_u_T(host)" % e2e_steps}
+           "call": "lbm_init_fields(host) + lbm_step(%d) + lbm_get_rho_u_T(host)" % e2e_steps,
+           "untimed_passes_before": 1}
 
     peak, peak_kind = measured_peaks()
     algo = BYTES_PER_NODE[args.prec] * N
