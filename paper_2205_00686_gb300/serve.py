@@ -184,10 +184,14 @@ class Server:
     """Admission by device memory + chunked continuous batching."""
 
     def __init__(self, backend, mem_budget: int, chunk: int = 100,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, pipeline: int = 1):
         self.backend = backend
         self.mem_budget = int(mem_budget)
         self.chunk = int(chunk)
+        # chunks queued ahead of the one the host waits for: with 2 the device
+        # keeps a chunk of work while the host's admissions and read-backs of
+        # one round outlast the chunk before it
+        self.pipeline = max(1, int(pipeline))
         self.clock = clock
         self.waiting: collections.deque = collections.deque()
         self.active: Dict[int, tuple] = {}       # rid -> (request, handle, bytes)
@@ -198,7 +202,7 @@ class Server:
         self.max_active = 0
         self._next = 0
         self.retiring = set()                    # rids whose steps are all queued
-        self._inflight = None                    # (token, [(rid, n)], at capacity) of the queued chunk
+        self._inflight = collections.deque()    # (token, [(rid, n)], at capacity) of the queued chunks
         # chunks queued while requests were still waiting for memory (the
         # device holds as much as the budget allows): their node updates and
         # the time from the previous chunk's completion to theirs
@@ -277,9 +281,9 @@ class Server:
         1. domains whose steps are all queued leave the batch (stream-ordered);
         2. waiting requests are admitted into the freed memory;
         3. the next chunk of steps is queued for the domains still running;
-        4. the previous chunk is waited for (the new one keeps the device
-           busy) and its error words are checked: a failed domain is retired
-           at once, alone;
+        4. the oldest queued chunk is waited for once more than `pipeline`
+           chunks are queued (the newer ones keep the device busy), and its
+           error words are checked: a failed domain is retired at once, alone;
         5. domains whose last step has completed are read back and retired.
 
         Returns False when there is nothing left to do."""
@@ -304,8 +308,10 @@ class Server:
                 r.planned += k
                 moved.append((rid, k))
             chunk = (token, moved, bool(self.waiting))
-        if self._inflight is not None:
-            token, members, at_cap = self._inflight
+        if chunk is not None:
+            self._inflight.append(chunk)
+        if self._inflight and (len(self._inflight) > self.pipeline or chunk is None):
+            token, members, at_cap = self._inflight.popleft()
             errs = self.backend.wait(token)
             now = self.clock()
             nodes = 0
@@ -323,12 +329,11 @@ class Server:
                 self._cap_nodes += nodes
                 self._cap_time += now - self._last_done
             self._last_done = now
-        self._inflight = chunk
         for rid in list(self.retiring):
             r = self.active[rid][0]
             if r.done_steps >= r.steps:
                 self._retire(rid)
-        return bool(self.active or self.waiting or self._inflight is not None)
+        return bool(self.active or self.waiting or self._inflight)
 
     def run(self, arrivals=None):
         """Runs until every request is done.  `arrivals` optionally lists

@@ -15,6 +15,18 @@ def _build():
     __graft_entry__.build()
 
 
+@pytest.fixture(autouse=True, params=[1, 2], ids=["pipeline1", "pipeline2"])
+def _pipeline(request, monkeypatch):
+    """Every test runs with one and with two chunks queued ahead."""
+    from paper_2205_00686_gb300.serve import Server
+    init = Server.__init__
+
+    def with_depth(self, *a, **k):
+        k.setdefault("pipeline", request.param)
+        init(self, *a, **k)
+    monkeypatch.setattr(Server, "__init__", with_depth)
+
+
 def requests():
     sides = [64, 96, 128, 80, 160, 112, 72]
     steps = [60, 45, 90, 30, 75, 50, 40]

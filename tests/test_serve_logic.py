@@ -9,6 +9,17 @@ import pytest
 from paper_2205_00686_gb300.serve import Server
 
 
+@pytest.fixture(autouse=True, params=[1, 2], ids=["pipeline1", "pipeline2"])
+def _pipeline(request, monkeypatch):
+    """Every test runs with one and with two chunks queued ahead."""
+    init = Server.__init__
+
+    def with_depth(self, *a, **k):
+        k.setdefault("pipeline", request.param)
+        init(self, *a, **k)
+    monkeypatch.setattr(Server, "__init__", with_depth)
+
+
 class FakeCase:
     def __init__(self, nx, ny, tag=0):
         self.nx, self.ny, self.tag = nx, ny, tag
