@@ -282,3 +282,34 @@ def test_set_path_refuses_a_negative_segment():
     d.set_path(True, 10 ** 6)            # clamped to the domain's planes
     assert d.path == (True, c.nz)
     d.close()
+
+
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "three_kernels"])
+@pytest.mark.parametrize("walls", [False, True])
+def test_two_planes_deep(walls, fused):
+    """nz = 2: between walls both planes touch a wall (each node's +z and -z
+    neighbours are the ghost layer or the other plane); periodic, each plane
+    is the other's neighbour on both sides.  FP64 against the oracle after
+    25 steps."""
+    import paper_2205_00686_gb300 as lbm
+    nx, ny, nz = 9, 7, 2
+    Tc = W.TC
+    sh = (nz, ny, nx)
+    p = W.params(gravity=1e-5)
+    rho = 0.3 * (1.0 + W.noise(6, sh, 1e-3))
+    T = 0.92 * Tc * (1.0 + W.noise(7, sh, 1e-3))
+    u = [W.noise(8 + i, sh, 1e-3) for i in range(3)]
+    bc = W.wall_bc3(0.93 * Tc, 0.9 * Tc, theta_deg=70.0) if walls else W.periodic_bc3()
+    o = O.Sim3(nx, ny, nz, p, bc)
+    o.init(rho, *u, T)
+    o.step(25)
+    d = lbm.Domain3(nx, ny, nz, p, bc, prec="fp64")
+    d.set_path(fused, 0)
+    d.init_fields(rho, *u, T)
+    d.step(25)
+    e = fields_err(d, o)
+    assert max(e.values()) <= 1e-10, e
+    gf, gg, gP = d.populations()
+    of, og, oP = o.populations()
+    assert P.rel_err(gf, of) <= 1e-12 and P.rel_err(gg, og) <= 1e-12
+    d.close()
