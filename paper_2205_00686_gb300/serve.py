@@ -79,6 +79,7 @@ class CudaBackend:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.batches: Dict[tuple, object] = {}
         self.handles: Dict[int, tuple] = {}
+        self.handle_of: Dict[int, tuple] = {}   # id(domain) -> its handle
         self.attached: Dict[int, bool] = {}
         # with autotune_steps > 0, a batch's tile is chosen by
         # lbm_batch_autotune (trials of that many steps on a shadow batch of
@@ -118,6 +119,7 @@ class CudaBackend:
         self.batches[key].attach(d)
         h = (d, buf, key, own)
         self.handles[id(h)] = h
+        self.handle_of[id(d)] = h
         self.attached[id(h)] = True
         return h
 
@@ -135,16 +137,10 @@ class CudaBackend:
             b.step(n)
             errs = torch.zeros(len(b), dtype=torch.int32).pin_memory()
             b.errors_async(errs.data_ptr())
-            parts.append((errs, [id(self._handle_of(d)) for d in b.members]))
+            parts.append((errs, [id(self.handle_of[id(d)]) for d in b.members]))
         ev = torch.cuda.Event()
         ev.record(self.stream)
         return ev, parts
-
-    def _handle_of(self, d):
-        for h in self.handles.values():
-            if h[0] is d:
-                return h
-        raise KeyError("domain without a handle")
 
     def wait(self, token) -> Dict[int, int]:
         """Waits for the chunk of `token` only; returns {id(handle): error}
@@ -169,6 +165,7 @@ class CudaBackend:
         self.detach(handle)
         d, buf, key, own = handle
         self.handles.pop(id(handle), None)
+        self.handle_of.pop(id(d), None)
         self.attached.pop(id(handle), None)
         out = None
         try:
